@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the rasterised SMoE fit step on GB300.
+
+One step = one fit iteration of the whole hot path on one image: binning
+(bounding boxes, prefix sum, scatter, per-tile sort), the fused per-tile
+forward render + MSE + backward, and finalize + Adam.  Workload (default):
+2048x2048 RGB synthetic image (polygons with colour ramps + Perlin texture),
+K = 262144 anisotropic kernels with linear experts, 16x16 tiles, q_max = 9.
+
+Metric: fwd+bwd pixel-kernel evaluations per second, where the evaluations of
+one step are sum over tiles of (in-image pixels of the tile) x (length of the
+tile's kernel list) -- the paper's per-block work count (FLOPs/pixel = 2 x
+average kernels per block, Tables I/II), counted once per forward+backward.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun): every rank fits its own image (replicas, weak scaling),
+no collective on the data path; rank 0 prints the job-wide line.
+The reference arm (--impl reference) times the CPU oracle as it stands on the
+host cores, on a bounded crop of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Gpix·kernel evals/s; fit p50/p99 latency at matched PSNR vs plain"
+UNIT = "Gpix·kernel evals/s"
+WORKLOAD = ("rgb2048_K262144_linear_aniso: 2048x2048 RGB fp32, 40 ramp polygons + Perlin "
+            "texture 0.1, K=262144 anisotropic kernels (area sigma 5 px, aspect 1-3), linear "
+            "experts, 16x16 tiles, q_max 9, Adam at the paper's rates")
+MUFU_PER_CLK_PER_SM = 16          # ex2 results per clock per SM (sm_80 .. sm_10x)
+# DRAM bytes per launch of the fused tile kernel from one ncu capture (see
+# profiles/); valid only while render.cu is the file that was profiled.
+TRAFFIC = {"render_cu_sha256": None, "bytes_per_launch": None}
+
+
+def sha256(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def evaluated_pairs(tile_off, W, H, T):
+    """sum over tiles of in-image pixels x list length (host, int64)."""
+    import numpy as np
+    tx, ty = (W + T - 1) // T, (H + T - 1) // T
+    lens = np.diff(tile_off.astype(np.int64))[: tx * ty].reshape(ty, tx)
+    pw = np.minimum(T, W - np.arange(tx) * T)
+    ph = np.minimum(T, H - np.arange(ty) * T)
+    return int((lens * ph[:, None] * pw[None, :]).sum())
+
+
+def crop_workload(wl, size):
+    """A size x size crop of a workload with the kernels whose centre lies in
+    it (same density, same list lengths) -- the oracle's bounded sample."""
+    import numpy as np
+    from paper_2510_05814_gb300 import synth
+    C, H, W = wl.target.shape
+    x0, y0 = (W - size) // 2, (H - size) // 2
+    t = wl.target[:, y0:y0 + size, x0:x0 + size].copy()
+    p = wl.params
+    px, py = p.mu[:, 0] * W - x0, p.mu[:, 1] * H - y0
+    sel = (px >= 0) & (px < size) & (py >= 0) & (py < size)
+    mu = np.stack([px[sel] / size, py[sel] / size], 1).astype(np.float32)
+    return t, synth.Params(mu, p.chol[sel].copy(), p.ea[sel].copy(),
+                           None if p.eW is None else p.eW[sel].copy())
+
+
+def oracle_sample(wl, size):
+    """Time the oracle (fwd + MSE backward, dense) on a crop; returns
+    (pairs in the metric's count, seconds, threads)."""
+    import oracle as om
+    t, p = crop_workload(wl, size)
+    m = om.Model(size, size, t.shape[0], p.mu, p.chol, p.ea, p.eW, tile=wl.tile, qmax=wl.qmax)
+    off, _ = om.bin_tiles(m)
+    pairs = evaluated_pairs(off, size, size, wl.tile)
+    t0 = time.perf_counter()
+    om.render(m)
+    om.backward(m, target=t)
+    return pairs, time.perf_counter() - t0, om.threads(), int(p.mu.shape[0])
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2510_05814_gb300 import synth
+    import oracle
+    oracle.build()
+    wl = synth.rgb_2048()
+    size = args.ref_crop
+    for _ in range(args.warmup):
+        oracle_sample(wl, size)
+    tot_pairs, tot_s, thr, kc = 0, 0.0, 1, 0
+    for _ in range(args.steps):
+        pairs, s, thr, kc = oracle_sample(wl, size)
+        tot_pairs += pairs
+        tot_s += s
+    value = tot_pairs / tot_s / 1e9
+    sample = (f"{size}x{size} centre crop of the 2048x2048 workload with its {kc} kernels; "
+              "dense oracle forward + MSE backward per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": thr, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-crop", type=int, default=512)
+    ap.add_argument("--ref-crop", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2510_05814_gb300 import build, synth
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2510_05814_gb300 import api
+    from paper_2510_05814_gb300.fit import FitBatch
+
+    wl = synth.rgb_2048(seed=3 + rank)
+    C, H, W = wl.target.shape
+    T = wl.tile
+    tgt = torch.tensor(wl.target, device="cuda")
+    params = api.SMoEParams.from_numpy(wl.params)
+    total_iters = args.warmup + 2 * args.steps + 4
+    fb = FitBatch([tgt], [params], total_iters, lr=synth.PAPER_LR, tile=T, qmax=wl.qmax,
+                  hist=total_iters)
+    desc = api.RasterDesc(W, H, C, T, True, wl.qmax, 1.0)
+
+    def pairs_now():
+        r = api.Rasterizer(desc, params.K, pair_cap=fb.pair_cap).bin(fb.params_of(0))
+        return evaluated_pairs(r.tile_off.cpu().numpy(), W, H, T), int(r.n_pairs.item())
+
+    for _ in range(args.warmup):
+        fb.launch(1)
+    torch.cuda.synchronize()
+    assert fb.status_code() == 0
+    pairs0, lists0 = pairs_now()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for s in range(args.steps):
+            flush.zero_()                       # L2 flush outside the timed region
+            e = ev[s]
+            e[0].record(stream)
+            fb.phase(0)
+            e[1].record(stream)
+            fb.phase(1)
+            e[2].record(stream)
+            fb.phase(2)
+            e[3].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    st = fb.status_code()
+    assert st == 0, f"fit status {st}"
+    bin_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    tile_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    adam_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    pairs1, lists1 = pairs_now()
+    pairs_step = 0.5 * (pairs0 + pairs1)
+    tot_s = sum(step_ms) / 1e3
+
+    # end to end through the public API with host buffers: per step the
+    # target goes host->device from pinned memory and the loss comes back.
+    host_t = torch.empty_like(tgt, device="cpu").pin_memory()
+    host_t.copy_(tgt.cpu())
+    host_loss = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(args.steps):
+        fb.targets[0].copy_(host_t, non_blocking=True)
+        it = int(args.warmup + args.steps + s)
+        fb.launch(1)
+        host_loss.copy_(fb.loss[0, it:it + 1], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    assert fb.status_code() == 0
+
+    # super-resolution render of the current model at 2x (4096 x 4096)
+    sr_desc = api.RasterDesc(2 * W, 2 * H, C, T, True, wl.qmax, 2.0)
+    sr = api.Rasterizer(sr_desc, params.K, pair_cap=4 * fb.pair_cap).bin(fb.params_of(0))
+    y_sr, inv_sr = sr.render()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    f0.record(stream)
+    sr.bin(fb.params_of(0), check_capacity=False)
+    sr.render(y_sr, inv_sr)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    sr_ms = f0.elapsed_time(f1)
+    sr_pairs = evaluated_pairs(sr.tile_off.cpu().numpy(), 2 * W, 2 * H, T)
+
+    # job-wide aggregation (max time over ranks, summed work)
+    vals = torch.tensor([tot_s, pairs_step * args.steps, e2e_s, sum(tile_ms) / 1e3],
+                        dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = vals.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm_ = vals.clone()
+        torch.distributed.all_reduce(sm_, op=torch.distributed.ReduceOp.SUM)
+        tot_s, work, e2e_s = float(mx[0]), float(sm_[1]), float(mx[2])
+    else:
+        work = pairs_step * args.steps
+    value = work / tot_s / 1e9
+    e2e_value = work / e2e_s / 1e9
+
+    clocks = clk.summary()
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = clocks.get("sm_max_mhz")
+    if not sm_max and os.path.exists(peaks_path):
+        sm_max = json.load(open(peaks_path)).get("sm_max_mhz")
+    sm_max = sm_max or 2070.0
+    ex2_peak = MUFU_PER_CLK_PER_SM * sms * sm_max * 1e6            # ex2 / s
+    tile_s = statistics.mean(tile_ms) / 1e3
+    ex2_achieved = 2.0 * pairs_step / tile_s                       # fwd + bwd: 2 ex2 / pair
+    traffic = None
+    if TRAFFIC["render_cu_sha256"] and TRAFFIC["render_cu_sha256"] == sha256(
+            os.path.join(ROOT, "paper_2510_05814_gb300", "csrc", "render.cu")):
+        traffic = TRAFFIC["bytes_per_launch"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        pairs_c, s_c, thr, kc = oracle_sample(wl, args.cpu_crop)
+        cpu = {"value": pairs_c / s_c / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{args.cpu_crop}x{args.cpu_crop} centre crop of the workload with its "
+                         f"{kc} kernels; one dense forward + MSE backward ({s_c:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "image": f"{W}x{H}x{C}", "K": params.K, "tile": T,
+                       "l2": "flushed (256 MiB write, untimed) before every timed step",
+                       "parallelism": f"replicas x{world}",
+                       "pairs_per_step": int(pairs_step), "list_pairs": int(lists1)},
+            "roofline": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
+                         "achieved": ex2_achieved / 1e9, "peak": ex2_peak / 1e9,
+                         "unit": "Gex2/s", "frac": ex2_achieved / ex2_peak,
+                         "traffic": traffic,
+                         "peak_basis": f"{MUFU_PER_CLK_PER_SM} ex2/clk/SM x {sms} SMs x "
+                                       f"{sm_max:.0f} MHz; 2 ex2 per fwd+bwd pair"},
+            "phases_ms": {"bin": statistics.mean(bin_ms), "fused_tiles": statistics.mean(tile_ms),
+                          "adam": statistics.mean(adam_ms)},
+            "fit_iters_per_s": args.steps / tot_s,
+            "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
+                             "Gpairs_per_s": sr_pairs / sr_ms / 1e6},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
+                    "d2h_bytes_per_step": 8},
+            "gpu_launches": 8 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

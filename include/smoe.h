@@ -1,0 +1,228 @@
+/*
+ * smoe.h -- C ABI of libsmoe.so: rasterised Steered Mixture of Experts (SMoE)
+ * image regression on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 2510.05814, "Rasterized Steered Mixture of Experts for
+ * Efficient 2D Image Regression"):
+ *   steered kernel   K_k(x) = exp(-1/2 (x-mu_k)^T L_k L_k^T (x-mu_k))   Eq. 2
+ *   softmax gate     w_k(x) = K_k(x) / sum_i K_i(x)   (pi_k = 1)          Eq. 4
+ *   regression       y(x)   = sum_{k in K_n} m_k(x) w_k(x)                Eqs. 3, 5
+ * where K_n is the list of kernels whose bounding box touches the tile n that
+ * holds x (Sec. IV-B "geometry shader", Sec. IV-C subset selection), and each
+ * kernel's support is truncated to q = ||L_k^T (x-mu_k)||^2 <= q_max (Sec. IV).
+ * The parameters are fitted by Adam on the MSE through the rasteriser
+ * (Sec. III-D, Sec. VI-B).  Resampling the fitted model on a finer raster is
+ * the native super-resolution of Sec. II-B / VII-C.
+ *
+ * Conventions shared by every entry point
+ *   - Pixel (i, j) is column i, row j; its centre is (i + 0.5, j + 0.5).
+ *   - Images are FP32, channel-planar C x H x W, contiguous.
+ *   - Parameters are FP32 structure-of-arrays (smoe_params): mu[K][2] in
+ *     normalised [0,1] image units (centre in pixels = mu * (W, H)),
+ *     chol[K][3] = (a, b, c) of L = [[a, 0], [b, c]] in pixel units of the
+ *     fitted raster, ea[K][C] expert offsets, eW[K][C][2] expert slopes
+ *     (linear experts m(x) = ea + eW (x - mu)); eW is NULL for constant
+ *     experts.  The sign of a and c is free (L L^T does not see it).
+ *   - Truncation predicate, evaluated in FP32 with one rounding per step:
+ *       dx = x0 - mx, dy = y0 - my, t = b*dy, z0 = fma(a, dx, t),
+ *       z1 = c*dy, q32 = fma(z0, z0, z1*z1);  included <=> q32 <= q_max.
+ *     A pixel with no included kernel renders 0 and has 1/D = 0.
+ *   - Bounding box: a square centred on mu with half side
+ *     r = sqrt(q_max * lambda_max(Sigma)) * (1 + 2^-10), clamped to the image
+ *     in tiles (Sec. IV-B, Fig. 3b); a kernel whose box is degenerate
+ *     (det = 0 or non-finite) is listed in every tile; a kernel with a
+ *     non-finite parameter is listed in none.
+ *   - Tile lists are CSR: tile_off[n_tiles + 1] (int32) and pair_k[] (int32),
+ *     tiles in row-major order, kernel ids ascending inside every tile.  The
+ *     lists are unique, so they are bit-exact across runs.
+ *
+ * Ownership and errors
+ *   - Every pointer argument marked (device) is GPU memory that the caller
+ *     owns; the library never allocates or frees device memory and never
+ *     synchronises except in smoe_get_status.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Argument errors and launch failures are returned synchronously.
+ *     Data-dependent failures (a pair count above pair_cap) are written to
+ *     the device status word (int32, 0 = OK) and every later kernel that sees
+ *     a non-zero status returns without work, so a captured CUDA graph stops
+ *     cleanly; read it with smoe_get_status.
+ */
+#ifndef SMOE_H
+#define SMOE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SMOE_API __attribute__((visibility("default")))
+#else
+#define SMOE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMOE_OK = 0,
+    SMOE_ERR_ARG = 1,        /* bad argument (sizes, NULL, alignment) */
+    SMOE_ERR_CAPACITY = 2,   /* pair count above pair_cap (device status) */
+    SMOE_ERR_CUDA = 3,       /* a CUDA call or launch failed */
+    SMOE_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    SMOE_ERR_WORKSPACE = 5   /* workspace too small or misaligned */
+} smoe_status;
+
+/* One raster. */
+typedef struct {
+    int32_t W, H;     /* raster size in pixels (the output raster for a render) */
+    int32_t C;        /* channels: 1 or 3 */
+    int32_t tile;     /* tile side in pixels: 8, 16 or 32 (Sec. IV-C uses 16) */
+    int32_t expert;   /* 0 = constant experts, 1 = linear experts */
+    float qmax;       /* truncation radius q_max (Mahalanobis, squared); 9 = 3 sigma */
+    float scale;      /* resampling scale s >= 0: L' = L / s, eW' = eW / s; 1 for a fit */
+} smoe_desc;
+
+/* Parameters (or gradients, or Adam moments) of K kernels, all device SoA. */
+typedef struct {
+    int64_t K;
+    float *mu;        /* K x 2 */
+    float *chol;      /* K x 3 */
+    float *ea;        /* K x C */
+    float *eW;        /* K x C x 2, NULL for constant experts */
+} smoe_params;
+
+/* Library version, (major << 16) | minor. */
+SMOE_API int32_t smoe_version(void);
+
+/* Bytes of device workspace that smoe_bin / smoe_render /
+ * smoe_render_backward need for this raster, K kernels and pair_cap pairs.
+ * The workspace must be 256-byte aligned. */
+SMOE_API smoe_status smoe_workspace_size(const smoe_desc *d, int64_t K, int64_t pair_cap,
+                                size_t *bytes);
+
+/* Geometry shader + subset kernel selection (Sec. IV-B, IV-C; Eq. 5).
+ * For every kernel: transform to output-pixel units, bounding box, tile
+ * rectangle; then a counting sort of (tile, kernel) pairs by tile: per-tile
+ * counts, an exclusive prefix sum (tile_off), an atomic scatter and a per-tile
+ * sort that restores ascending kernel order.  Also leaves the kernels'
+ * prepared records in `ws` for smoe_render / smoe_render_backward.
+ *   p          parameters (device SoA, K = p->K)
+ *   ws         workspace (device, smoe_workspace_size bytes)
+ *   tile_off   out: n_tiles + 1 int32 (device)
+ *   pair_k     out: pair_cap int32 (device)
+ *   n_pairs    out: one int64, the total pair count P (device)
+ *   status     in/out: one int32 (device); set to SMOE_ERR_CAPACITY if
+ *              P > pair_cap (the lists are then not written) */
+SMOE_API smoe_status smoe_bin(const smoe_desc *d, const smoe_params *p, void *ws, size_t ws_bytes,
+                     int32_t *tile_off, int32_t *pair_k, int64_t pair_cap,
+                     int64_t *n_pairs, int32_t *status, void *stream);
+
+/* Forward render per tile (Eqs. 2-5): y_c = N_c / D with N_c = sum e m_c,
+ * D = sum e over the tile's list, e = exp(-q/2) [q32 <= q_max].  FP32
+ * accumulation.  Reads the prepared records that smoe_bin left in `ws` (same
+ * desc and parameters).
+ *   y      out: C x H x W (device)
+ *   inv_d  out: H x W, 1/D (0 where D = 0), or NULL (device)
+ *   status in: skipped when non-zero (device) */
+SMOE_API smoe_status smoe_render(const smoe_desc *d, int64_t K, const void *ws, size_t ws_bytes,
+                        const int32_t *tile_off, const int32_t *pair_k,
+                        float *y, float *inv_d, const int32_t *status, void *stream);
+
+/* Backward of smoe_render (the gradient-descent fit through the rasteriser,
+ * Sec. III-D): gradients of a loss L w.r.t. mu, chol, ea, eW, ADDED into
+ * `grad` (caller zeroes it).  Upstream: gy = dL/dy (C x H x W) or, if gy is
+ * NULL, the MSE sum((y - target)^2) / (C H W) against `target`.  Gates are
+ * recomputed from the lists; y and inv_d are the outputs of smoe_render.
+ * Per-kernel partial sums are accumulated with atomics in `ws`, so the result
+ * is deterministic only up to FP32 summation order. */
+SMOE_API smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params *p, void *ws,
+                                 size_t ws_bytes, const int32_t *tile_off,
+                                 const int32_t *pair_k, const float *y, const float *inv_d,
+                                 const float *gy, const float *target,
+                                 const smoe_params *grad, const int32_t *status,
+                                 void *stream);
+
+/* Adam (Sec. VI-B), torch semantics, FP32, one fused launch over the four
+ * parameter groups; zeroes g.  lr = {mu, chol, ea, eW}; step >= 1 is the
+ * 1-based step used for the bias corrections.  C is the channel count
+ * (sizes of ea / eW).  eW pointers must all be NULL or all non-NULL. */
+SMOE_API smoe_status smoe_adam_step(const smoe_params *p, const smoe_params *g, const smoe_params *m,
+                           const smoe_params *v, int32_t C, const float lr[4], float b1,
+                           float b2, float eps, int32_t step, void *stream);
+
+/* Sum of squared differences over n floats, FP64 accumulation, ADDED to
+ * *out (device); with clamp != 0, y is clamped to [0, 1] first (the PSNR
+ * convention). */
+SMOE_API smoe_status smoe_sq_error(const float *y, const float *target, int64_t n, int32_t clamp,
+                          double *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Fit: a batch of B images (B = 1 for a single image), one iteration =      */
+/* bin -> fused forward/backward per tile (MSE) -> finalize + Adam.          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t W, H;           /* image size */
+    int64_t K;              /* kernels of this image */
+    int64_t k_off;          /* first kernel of this image in the batch's SoA arrays */
+    const float *target;    /* C x H x W (device) */
+    int32_t iters;          /* length of this image's run (lr schedule, loss history) */
+    float lr_mu0, lr_mu1;   /* centre rate, decayed exponentially lr_mu0 -> lr_mu1 */
+    float lr_chol, lr_ea, lr_eW;
+} smoe_fit_image;
+
+typedef struct {
+    int32_t B;              /* images */
+    int32_t C, tile, expert;
+    float qmax;
+    float b1, b2, eps;      /* Adam */
+    smoe_params p, m, v;    /* batch SoA (device): K_total kernels, image b at k_off */
+    int32_t *step;          /* device, B: iterations done per image (caller-owned) */
+    double *loss;           /* device, B x hist: MSE per image and iteration, or NULL */
+    int32_t hist;           /* columns of `loss` */
+} smoe_fit_batch;
+
+/* Workspace bytes for a fit of this batch with pair_cap pairs in total. */
+SMOE_API smoe_status smoe_fit_workspace_size(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                    int64_t pair_cap, size_t *bytes);
+
+/* Prepare a fit: writes the batch table into `ws` (one host-to-device copy
+ * on `stream`, after which the stream is synchronised once) and zeroes the
+ * workspace's gradient sums.  With reset != 0 it also zeroes the Adam moments
+ * m and v, the step counters, the loss history and the status word, i.e.
+ * starts every image's run from iteration 0; with reset == 0 a run continues
+ * (e.g. after re-initialising with a larger pair_cap).  Call outside stream
+ * capture. */
+SMOE_API smoe_status smoe_fit_init(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                          int64_t pair_cap, void *ws, size_t ws_bytes, int32_t reset,
+                          int32_t *status, void *stream);
+
+/* Run n_iters fit iterations of the batch prepared in `ws` by smoe_fit_init
+ * with the same batch, imgs and pair_cap.  One iteration = binning of all
+ * images' kernels, one fused forward/MSE/backward launch over all tiles of all
+ * images (a ragged tile table), and one fused finalize + Adam launch.  No host
+ * synchronisation, so iterations can be captured in a CUDA graph and
+ * replayed.  Image b stops updating after imgs[b].iters iterations; the MSE
+ * of its iteration i (before that iteration's update) is written to
+ * loss[b * hist + i] when i < hist. */
+SMOE_API smoe_status smoe_fit(const smoe_fit_batch *batch, const smoe_fit_image *imgs, int64_t pair_cap,
+                     void *ws, size_t ws_bytes, int32_t n_iters, int32_t *status,
+                     void *stream);
+
+/* One phase of one fit iteration (the iteration of smoe_fit is phases 0, 1,
+ * 2 in this order): 0 = binning of all images' kernels, 1 = the fused
+ * forward / MSE / backward launch over the ragged tile table, 2 = finalize +
+ * Adam (advances the step counters).  Lets a caller place or time the phases
+ * separately; the three in order are exactly one smoe_fit iteration. */
+SMOE_API smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                    int64_t pair_cap, void *ws, size_t ws_bytes, int32_t phase,
+                                    int32_t *status, void *stream);
+
+/* Synchronise `stream` and return the device status word (SMOE_OK, or the
+ * first data-dependent error), or SMOE_ERR_CUDA if the stream failed. */
+SMOE_API smoe_status smoe_get_status(const int32_t *status, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMOE_H */

@@ -61,7 +61,7 @@ def _load():
         lib.om_rect.restype = I64
         lib.om_bin.argtypes = [MP, I64, P, P, P, I64]
         lib.om_bin.restype = I64
-        lib.om_render.argtypes = [MP, I64, P, P, P]
+        lib.om_render.argtypes = [MP, I64, P, P, P, P]
         lib.om_render.restype = None
         lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P]
         lib.om_backward.restype = None
@@ -161,19 +161,22 @@ def bin_tiles(m: Model, tiles=None):
     return off, pk[:total]
 
 
-def render(m: Model, pixels=None):
+def render(m: Model, pixels=None, with_scale=False):
     """FP64 render.  Returns (y, invd): y is (C,H,W) for a full render or
-    (C,n) for the listed flat pixel indices; invd likewise (H,W) or (n,)."""
+    (C,n) for the listed flat pixel indices; invd likewise (H,W) or (n,).
+    with_scale=True also returns sum_k w_k |m_k| in y's layout."""
     lib = _load()
     c = m._c()
     sel = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)
     n = m.W * m.H if sel is None else len(sel)
     y = np.zeros((m.C, n), np.float64)
     invd = np.zeros(n, np.float64)
-    lib.om_render(ctypes.byref(c), n, _ptr(sel), _ptr(y), _ptr(invd))
+    absm = np.zeros((m.C, n), np.float64) if with_scale else None
+    lib.om_render(ctypes.byref(c), n, _ptr(sel), _ptr(y), _ptr(invd), _ptr(absm))
     if sel is None:
-        return y.reshape(m.C, m.H, m.W), invd.reshape(m.H, m.W)
-    return y, invd
+        y, invd = y.reshape(m.C, m.H, m.W), invd.reshape(m.H, m.W)
+        absm = None if absm is None else absm.reshape(m.C, m.H, m.W)
+    return (y, invd, absm) if with_scale else (y, invd)
 
 
 def backward(m: Model, gy=None, target=None, kernels=None):

@@ -216,18 +216,22 @@ static void pair_value(const om_model *m, int64_t k, int32_t i, int32_t j,
     }
 }
 
-/* Gate denominator D and numerators N_c at one pixel over all K kernels. */
+/* Gate denominator D and numerators N_c at one pixel over all K kernels;
+ * A_c (if non-NULL) receives sum_k e_k |m_kc|, the scale of the sum. */
 static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
-                       double *N)
+                       double *N, double *A)
 {
     double d = 0.0;
-    for (int ch = 0; ch < m->C; ++ch) N[ch] = 0.0;
+    for (int ch = 0; ch < m->C; ++ch) { N[ch] = 0.0; if (A) A[ch] = 0.0; }
     for (int64_t k = 0; k < m->K; ++k) {
         if (!om_included(m, k, i, j)) continue;
         om_pair pr;
         pair_value(m, k, i, j, &pr);
         d += pr.e;
-        for (int ch = 0; ch < m->C; ++ch) N[ch] += pr.e * pr.mexp[ch];
+        for (int ch = 0; ch < m->C; ++ch) {
+            N[ch] += pr.e * pr.mexp[ch];
+            if (A) A[ch] += pr.e * fabs(pr.mexp[ch]);
+        }
     }
     *D = d;
 }
@@ -235,19 +239,23 @@ static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
 /* Forward render (Eqs. 2-5): y_c = N_c / D, invd = 1/D; a pixel with no
  * included kernel (D = 0) gets y = 0 and invd = 0.  px == NULL renders all
  * H*W pixels in row-major order; otherwise the n_px listed flat pixel indices
- * (j*W + i).  y is channel-planar over the rendered pixels: y[c*n + p]. */
+ * (j*W + i).  y is channel-planar over the rendered pixels: y[c*n + p].
+ * absm (optional, same layout as y) receives sum_k w_k |m_kc|, the size of
+ * the terms of the gated sum (used to scale a tolerance). */
 void om_render(const om_model *m, int64_t n_px, const int64_t *px, double *y,
-               double *invd)
+               double *invd, double *absm)
 {
     int64_t n = px ? n_px : (int64_t)m->W * m->H;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t p = 0; p < n; ++p) {
         int64_t f = px ? px[p] : p;
         int32_t i = (int32_t)(f % m->W), j = (int32_t)(f / m->W);
-        double D, N[3];
-        pixel_sums(m, i, j, &D, N);
-        for (int ch = 0; ch < m->C; ++ch)
+        double D, N[3], A[3];
+        pixel_sums(m, i, j, &D, N, A);
+        for (int ch = 0; ch < m->C; ++ch) {
             y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;
+            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / D : 0.0;
+        }
         if (invd) invd[p] = D > 0.0 ? 1.0 / D : 0.0;
     }
 }
@@ -291,7 +299,7 @@ void om_backward(const om_model *m, const double *gy, const float *target,
         if (!need[p]) continue;
         int32_t i = (int32_t)(p % m->W), j = (int32_t)(p / m->W);
         double d, N[3];
-        pixel_sums(m, i, j, &d, N);
+        pixel_sums(m, i, j, &d, N, NULL);
         D[p] = d;
         for (int ch = 0; ch < C; ++ch) {
             double yv = d > 0.0 ? N[ch] / d : 0.0;
@@ -410,7 +418,7 @@ void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[5],
         for (int gi = 0; gi < 4; ++gi)
             for (int64_t x = 0; x < n_g[gi]; ++x) fp[gi][x] = (float)P[gi][x];
         if (loss) {
-            om_render(m, 0, NULL, y, NULL);
+            om_render(m, 0, NULL, y, NULL, NULL);
             double se = 0.0;
             for (int64_t x = 0; x < HW * C; ++x) {
                 double d = y[x] - (double)target[x];

@@ -1,0 +1,250 @@
+"""Python binding of libsmoe.so: the C-ABI calls under the same names, taking
+torch CUDA tensors (argument marshalling only -- every step runs in the
+library's kernels), plus small helpers that own workspaces and lists."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SmoeError, check
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+@dataclass(frozen=True)
+class RasterDesc:
+    """A raster: W x H pixels, C channels, tile side, expert type, cutoff and
+    resampling scale (L' = L/s, eW' = eW/s)."""
+    W: int
+    H: int
+    C: int
+    tile: int = 16
+    linear: bool = True
+    qmax: float = 9.0
+    scale: float = 1.0
+
+    def c(self):
+        return _lib.Desc(self.W, self.H, self.C, self.tile, int(self.linear), self.qmax, self.scale)
+
+    @property
+    def n_tiles(self):
+        return ((self.W + self.tile - 1) // self.tile) * ((self.H + self.tile - 1) // self.tile)
+
+
+class SMoEParams:
+    """Kernel parameters as FP32 CUDA tensors (SoA): mu (K,2) normalised,
+    chol (K,3) = (a,b,c), ea (K,C), eW (K,C,2) or None."""
+
+    def __init__(self, mu, chol, ea, eW=None):
+        self.mu, self.chol, self.ea, self.eW = mu, chol, ea, eW
+
+    @classmethod
+    def from_numpy(cls, p, device="cuda"):
+        f = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a, np.float32),
+                                                              device=device)
+        return cls(f(p.mu), f(p.chol), f(p.ea), f(p.eW))
+
+    @classmethod
+    def zeros(cls, K, C, linear, device="cuda"):
+        z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=device)
+        return cls(z(K, 2), z(K, 3), z(K, C), z(K, C, 2) if linear else None)
+
+    def zeros_like(self):
+        return SMoEParams(*(None if t is None else torch.zeros_like(t) for t in self.tensors()))
+
+    def clone(self):
+        return SMoEParams(*(None if t is None else t.clone() for t in self.tensors()))
+
+    def tensors(self):
+        return (self.mu, self.chol, self.ea, self.eW)
+
+    @property
+    def K(self):
+        return int(self.mu.shape[0])
+
+    @property
+    def C(self):
+        return int(self.ea.shape[1])
+
+    @property
+    def linear(self):
+        return self.eW is not None
+
+    def c(self):
+        return _lib.Params(self.K, _ptr(self.mu), _ptr(self.chol), _ptr(self.ea), _ptr(self.eW))
+
+    def numpy(self):
+        return tuple(None if t is None else t.detach().cpu().numpy() for t in self.tensors())
+
+
+# ---------------------------------------------------------------------------
+# the C-ABI calls
+# ---------------------------------------------------------------------------
+
+def smoe_version() -> int:
+    return int(_lib.load().smoe_version())
+
+
+def smoe_workspace_size(desc: RasterDesc, K: int, pair_cap: int) -> int:
+    n = ctypes.c_size_t(0)
+    check(_lib.load().smoe_workspace_size(ctypes.byref(desc.c()), K, pair_cap, ctypes.byref(n)),
+          "smoe_workspace_size")
+    return int(n.value)
+
+
+def smoe_bin(desc, params: SMoEParams, ws, tile_off, pair_k, n_pairs, status, stream=None):
+    d, p = desc.c(), params.c()
+    check(_lib.load().smoe_bin(ctypes.byref(d), ctypes.byref(p), _ptr(ws), ws.numel(),
+                               _ptr(tile_off), _ptr(pair_k), pair_k.numel(), _ptr(n_pairs),
+                               _ptr(status), _stream(stream)), "smoe_bin")
+
+
+def smoe_render(desc, K, ws, tile_off, pair_k, y, inv_d=None, status=None, stream=None):
+    d = desc.c()
+    check(_lib.load().smoe_render(ctypes.byref(d), K, _ptr(ws), ws.numel(), _ptr(tile_off),
+                                  _ptr(pair_k), _ptr(y), _ptr(inv_d), _ptr(status),
+                                  _stream(stream)), "smoe_render")
+
+
+def smoe_render_backward(desc, params, ws, tile_off, pair_k, y, inv_d, gy, target, grad,
+                         status=None, stream=None):
+    d, p, g = desc.c(), params.c(), grad.c()
+    check(_lib.load().smoe_render_backward(ctypes.byref(d), ctypes.byref(p), _ptr(ws), ws.numel(),
+                                           _ptr(tile_off), _ptr(pair_k), _ptr(y), _ptr(inv_d),
+                                           _ptr(gy), _ptr(target), ctypes.byref(g), _ptr(status),
+                                           _stream(stream)), "smoe_render_backward")
+
+
+def smoe_adam_step(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1, stream=None):
+    lr4 = (ctypes.c_float * 4)(*[float(x) for x in lr])
+    pc, gc, mc, vc = p.c(), g.c(), m.c(), v.c()
+    check(_lib.load().smoe_adam_step(ctypes.byref(pc), ctypes.byref(gc), ctypes.byref(mc),
+                                     ctypes.byref(vc), p.C, lr4, b1, b2, eps, step,
+                                     _stream(stream)), "smoe_adam_step")
+
+
+def smoe_sq_error(y, target, out, clamp=True, stream=None):
+    check(_lib.load().smoe_sq_error(_ptr(y), _ptr(target), y.numel(), int(clamp), _ptr(out),
+                                    _stream(stream)), "smoe_sq_error")
+
+
+def smoe_get_status(status, stream=None) -> int:
+    return int(_lib.load().smoe_get_status(_ptr(status), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+class Rasterizer:
+    """Owns the workspace, the tile lists and the status word of one raster.
+
+    ``bin`` builds the lists (growing the pair buffer when the pair count
+    exceeds it, which costs one host synchronisation), ``render`` and
+    ``backward`` run the tile kernels on them."""
+
+    def __init__(self, desc: RasterDesc, K: int, pair_cap: int | None = None, device="cuda"):
+        self.desc, self.K, self.device = desc, K, device
+        self.tile_off = torch.zeros(desc.n_tiles + 1, dtype=torch.int32, device=device)
+        self.n_pairs = torch.zeros(1, dtype=torch.int64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self._alloc(pair_cap if pair_cap is not None else max(1024, 8 * K))
+
+    def _alloc(self, cap):
+        self.pair_cap = int(cap)
+        self.pair_k = torch.zeros(max(self.pair_cap, 1), dtype=torch.int32, device=self.device)
+        n = smoe_workspace_size(self.desc, self.K, self.pair_cap)
+        self.ws = torch.empty(n + 256, dtype=torch.uint8, device=self.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws = self.ws[off:off + n]
+
+    def bin(self, params: SMoEParams, check_capacity=True, stream=None):
+        assert params.K == self.K
+        self.status.zero_()
+        smoe_bin(self.desc, params, self.ws, self.tile_off, self.pair_k, self.n_pairs, self.status,
+                 stream)
+        if check_capacity:
+            st = smoe_get_status(self.status, stream)
+            if st == _lib.SMOE_ERR_CAPACITY:
+                need = int(self.n_pairs.item())
+                self._alloc(int(need * 1.25) + 1024)
+                self.status.zero_()
+                smoe_bin(self.desc, params, self.ws, self.tile_off, self.pair_k, self.n_pairs,
+                         self.status, stream)
+                st = smoe_get_status(self.status, stream)
+            if st != _lib.SMOE_OK:
+                raise SmoeError(st, "smoe_bin")
+        return self
+
+    def render(self, y=None, inv_d=None, stream=None):
+        d = self.desc
+        if y is None:
+            y = torch.empty(d.C, d.H, d.W, dtype=torch.float32, device=self.device)
+        if inv_d is None:
+            inv_d = torch.empty(d.H, d.W, dtype=torch.float32, device=self.device)
+        smoe_render(d, self.K, self.ws, self.tile_off, self.pair_k, y, inv_d, self.status, stream)
+        return y, inv_d
+
+    def backward(self, params, y, inv_d, gy=None, target=None, grad=None, stream=None):
+        if grad is None:
+            grad = params.zeros_like()
+        smoe_render_backward(self.desc, params, self.ws, self.tile_off, self.pair_k, y, inv_d, gy,
+                             target, grad, self.status, stream)
+        return grad
+
+    def lists(self):
+        """(tile_off, pair_k) trimmed to the pair count, on the host."""
+        off = self.tile_off.cpu().numpy()
+        return off, self.pair_k[: int(off[-1])].cpu().numpy()
+
+
+def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0):
+    """Bin and render ``params`` on a W x H raster; returns (y, inv_d, rasterizer)."""
+    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, scale)
+    r = Rasterizer(desc, params.K).bin(params)
+    y, inv_d = r.render()
+    return y, inv_d, r
+
+
+class SMoERender(torch.autograd.Function):
+    """y = R-SMoE render of (mu, chol, ea, eW) on a raster (Eqs. 2-5), with the
+    backward of the tile kernels.  Each forward keeps its own lists for its
+    backward."""
+
+    @staticmethod
+    def forward(ctx, mu, chol, ea, eW, desc: RasterDesc):
+        p = SMoEParams(mu.detach().contiguous(), chol.detach().contiguous(),
+                       ea.detach().contiguous(), None if eW is None else eW.detach().contiguous())
+        r = Rasterizer(desc, p.K).bin(p)
+        y, inv_d = r.render()
+        ctx.r, ctx.p = r, p
+        ctx.save_for_backward(y, inv_d)
+        ctx.has_w = eW is not None
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        y, inv_d = ctx.saved_tensors
+        g = ctx.r.backward(ctx.p, y, inv_d, gy=gy.contiguous())
+        return g.mu, g.chol, g.ea, (g.eW if ctx.has_w else None), None
+
+
+def smoe_render_fn(mu, chol, ea, eW, desc: RasterDesc):
+    return SMoERender.apply(mu, chol, ea, eW, desc)

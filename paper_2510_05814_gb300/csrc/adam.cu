@@ -1,0 +1,193 @@
+// Adam (Sec. VI-B: all groups optimised with Adam; per-group learning rates;
+// the centre rate decays exponentially over the run), torch semantics in FP32:
+//   m <- m + (1 - b1) (g - m);  v <- b2 v + (1 - b2) g^2
+//   p <- p - (lr / (1 - b1^t)) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+#include <cmath>
+
+#include "smoe_internal.cuh"
+
+namespace smoe {
+
+namespace {
+
+struct AdamK {
+    float b1, b2, eps;
+    float step_size;       // lr / (1 - b1^t)
+    float inv_sqrt_bc2;    // 1 / sqrt(1 - b2^t)
+};
+
+__device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, const AdamK &k) {
+    m = fmaf(1.0f - k.b1, g - m, m);
+    v = fmaf(k.b2, v, (1.0f - k.b2) * g * g);
+    const float denom = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
+    p -= k.step_size * (m / denom);
+}
+
+// One launch over the four groups of a SoA parameter set; zeroes g.
+__global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_params gr,
+                           smoe_params m, smoe_params v, float lr0, float lr1, float lr2,
+                           float lr3, float b1, float b2, float eps, float bc1, float isb2) {
+    const int64_t n_mu = 2 * K, n_ch = 3 * K, n_ea = (int64_t)C * K;
+    const int64_t n_w = has_w ? 2 * (int64_t)C * K : 0;
+    const int64_t total = n_mu + n_ch + n_ea + n_w;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float *pp, *gg, *mm, *vv;
+        float lr;
+        int64_t x = i;
+        if (x < n_mu) { pp = p.mu; gg = gr.mu; mm = m.mu; vv = v.mu; lr = lr0; }
+        else if ((x -= n_mu) < n_ch) { pp = p.chol; gg = gr.chol; mm = m.chol; vv = v.chol; lr = lr1; }
+        else if ((x -= n_ch) < n_ea) { pp = p.ea; gg = gr.ea; mm = m.ea; vv = v.ea; lr = lr2; }
+        else { x -= n_ea; pp = p.eW; gg = gr.eW; mm = m.eW; vv = v.eW; lr = lr3; }
+        AdamK k{b1, b2, eps, lr / bc1, isb2};
+        float pv = pp[x], mv = mm[x], vv_ = vv[x];
+        adam1(pv, gg[x], mv, vv_, k);
+        pp[x] = pv; mm[x] = mv; vv[x] = vv_;
+        gg[x] = 0.0f;
+    }
+}
+
+// Fit: raw per-kernel sums -> gradients (see render.cu) -> Adam on the 5 + C
+// (+ 2C) parameters of the kernel; zeroes the sums.  The last CTA to finish
+// advances every running image's step counter.
+__global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, float *chol,
+                           float *ea, float *eW, float *m_mu, float *m_chol, float *m_ea,
+                           float *m_eW, float *v_mu, float *v_chol, float *v_ea, float *v_eW,
+                           float b1, float b2, float eps, int32_t *step, uint32_t *done) {
+    if (status_bad(w.status)) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < g.K_total) {
+        const int b = img_by_kernel(g, k);
+        const ImgDev &im = img_of(g, b);
+        const int32_t it = step[b];
+        if (it < im.iters) {
+            // A kernel listed in no tile touched no pixel: its gradient is 0
+            // (and must not become inf * 0 for non-finite parameters).
+            const int4 rc = w.rect[k];
+            float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
+                              0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float *acc = w.acc + k * g.GS;
+            const float *s = rc.x <= rc.z ? acc : zero;
+            const float *r = w.rec + k * g.S;
+            const int C = g.C, E = g.linear ? 3 : 1;
+            const float t = (float)(it + 1);
+            const float bc1 = 1.0f - powf(b1, t);
+            const float isb2 = rsqrtf(1.0f - powf(b2, t));
+            const float f = im.iters > 1 ? (float)it / (float)(im.iters - 1) : 0.0f;
+            const float lr_mu = im.lr_mu0 * powf(im.lr_mu1 / im.lr_mu0, f);
+            AdamK kmu{b1, b2, eps, lr_mu / bc1, isb2};
+            AdamK kch{b1, b2, eps, im.lr_chol / bc1, isb2};
+            AdamK kea{b1, b2, eps, im.lr_ea / bc1, isb2};
+            AdamK kew{b1, b2, eps, im.lr_eW / bc1, isb2};
+            float gmx = 0.f, gmy = 0.f;
+            if (rc.x <= rc.z) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
+            for (int ch = 0; ch < C; ++ch) {
+                const int64_t x = k * C + ch;
+                float pv = ea[x], mv = m_ea[x], vv = v_ea[x];
+                adam1(pv, s[5 + ch], mv, vv, kea);
+                ea[x] = pv; m_ea[x] = mv; v_ea[x] = vv;
+                if (g.linear) {
+                    if (rc.x <= rc.z) {
+                        gmx -= r[7 + ch * E + 1] * s[5 + ch];
+                        gmy -= r[7 + ch * E + 2] * s[5 + ch];
+                    }
+                    for (int d = 0; d < 2; ++d) {
+                        const int64_t xw = x * 2 + d;
+                        float pw = eW[xw], mw = m_eW[xw], vw = v_eW[xw];
+                        adam1(pw, s[5 + (1 + d) * C + ch], mw, vw, kew);
+                        eW[xw] = pw; m_eW[xw] = mw; v_eW[xw] = vw;
+                    }
+                }
+            }
+            const float gm[2] = {gmx * (float)im.W, gmy * (float)im.H};
+            for (int d = 0; d < 2; ++d) {
+                float pv = mu[2 * k + d], mv = m_mu[2 * k + d], vv = v_mu[2 * k + d];
+                adam1(pv, gm[d], mv, vv, kmu);
+                mu[2 * k + d] = pv; m_mu[2 * k + d] = mv; v_mu[2 * k + d] = vv;
+            }
+            for (int d = 0; d < 3; ++d) {
+                float pv = chol[3 * k + d], mv = m_chol[3 * k + d], vv = v_chol[3 * k + d];
+                adam1(pv, -s[d], mv, vv, kch);
+                chol[3 * k + d] = pv; m_chol[3 * k + d] = mv; v_chol[3 * k + d] = vv;
+            }
+            for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
+        }
+    }
+    // Step counters advance once every CTA has read them.
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(done, 1u);
+        last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        for (int b = 0; b < g.B; ++b)
+            if (step[b] < img_of(g, b).iters) step[b] += 1;
+        *done = 0u;
+        __threadfence();
+    }
+}
+
+__global__ void k_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float v = y[i];
+        if (clamp) v = fminf(fmaxf(v, 0.0f), 1.0f);
+        const double d = (double)v - (double)t[i];
+        s += d * d;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += ws[i];
+        atomicAdd(out, a);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
+                            const smoe_params &v, int C, const float lr[4], float b1, float b2,
+                            float eps, int32_t step, cudaStream_t st) {
+    const int has_w = p.eW != nullptr;
+    const int64_t total = p.K * (5 + (int64_t)C * (has_w ? 3 : 1));
+    if (total == 0) return cudaSuccess;
+    const double bc1 = 1.0 - std::pow((double)b1, (double)step);
+    const double isb2 = 1.0 / std::sqrt(1.0 - std::pow((double)b2, (double)step));
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_adam_soa<<<(unsigned)blocks, 256, 0, st>>>(p.K, C, has_w, p, gr, m, v, lr[0], lr[1],
+                                                 lr[2], lr[3], b1, b2, eps, (float)bc1,
+                                                 (float)isb2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
+                            float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
+                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, float b1,
+                            float b2, float eps, int32_t *step, uint32_t *done,
+                            cudaStream_t st) {
+    const unsigned blocks = (unsigned)((g.K_total + 255) / 256);
+    if (blocks == 0) return cudaSuccess;
+    k_fit_adam<<<blocks, 256, 0, st>>>(g, w, mu, chol, ea, eW, m_mu, m_chol, m_ea, m_eW, v_mu,
+                                       v_chol, v_ea, v_eW, b1, b2, eps, step, done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_sq_error<<<(unsigned)blocks, 256, 0, st>>>(y, t, n, clamp, out);
+    return cudaGetLastError();
+}
+
+}  // namespace smoe

@@ -1,0 +1,324 @@
+// Binning: the "geometry shader" (Sec. IV-B) and the subset kernel selection
+// per block (Sec. IV-C, Eq. 5) as a counting sort of (tile, kernel) pairs.
+//
+//   k_prep_bbox   one thread per kernel: prepared record, tile rectangle,
+//                 per-tile counts (atomic increments)
+//   k_scan_*      exclusive prefix sum of the per-tile counts -> tile_off
+//                 (three phases: block sums, scan of the sums, block scans)
+//   k_scatter     one thread per kernel: claim a slot in each covered tile
+//   k_segsort     one CTA per tile: restore ascending kernel order inside the
+//                 tile (bitonic sort in shared memory, or a bitmap sweep over
+//                 the kernel-id range for very long lists)
+//
+// The per-tile lists are the unique sets {k : tile in rect_k} in ascending k,
+// so the output is bit-exact whatever order the atomics took.
+#include "smoe_internal.cuh"
+
+namespace smoe {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256;
+constexpr int kSortMax = 2048;                 // bitonic in shared memory up to this
+constexpr int kBitmapWords = 8192;             // 262144 kernel ids per bitmap pass
+
+__global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
+    if (status_bad(w.status)) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= g.K_total) return;
+    const ImgDev &im = img_of(g, img_by_kernel(g, k));
+    // Kernel in output-pixel units, one rounding per operation.
+    float mx = __fmul_rn(g.mu[2 * k], (float)im.W);
+    float my = __fmul_rn(g.mu[2 * k + 1], (float)im.H);
+    float a = g.chol[3 * k], b = g.chol[3 * k + 1], c = g.chol[3 * k + 2];
+    const bool scaled = g.scale != 1.0f;
+    if (scaled) {
+        a = __fdiv_rn(a, g.scale);
+        b = __fdiv_rn(b, g.scale);
+        c = __fdiv_rn(c, g.scale);
+    }
+    float *r = w.rec + k * g.S;
+    r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c; r[5] = 0.0f; r[6] = 0.0f;
+    const int E = g.linear ? 3 : 1;
+    for (int ch = 0; ch < g.C; ++ch) {
+        r[7 + ch * E] = g.ea[k * g.C + ch];
+        if (g.linear) {
+            float w0 = g.eW[(k * g.C + ch) * 2], w1 = g.eW[(k * g.C + ch) * 2 + 1];
+            if (scaled) { w0 = __fdiv_rn(w0, g.scale); w1 = __fdiv_rn(w1, g.scale); }
+            r[7 + ch * E + 1] = w0;
+            r[7 + ch * E + 2] = w1;
+        }
+    }
+    for (int x = 7 + g.C * E; x < g.S; ++x) r[x] = 0.0f;
+
+    // Bounding box: square of half side r = sqrt(q_max * lambda_max(Sigma))
+    // * (1 + 2^-10), lambda_max(Sigma) = lambda_max(P) / det(P), P = L L^T.
+    int4 rect = make_int4(0, 0, -1, -1);
+    const bool finite = isfinite(mx) && isfinite(my) && isfinite(a) && isfinite(b) && isfinite(c);
+    if (finite) {
+        float p00 = __fmul_rn(a, a);
+        float p01 = __fmul_rn(a, b);
+        float cc = __fmul_rn(c, c);
+        float p11 = __fmaf_rn(b, b, cc);
+        float h = __fmul_rn(0.5f, __fsub_rn(p00, p11));
+        float p01sq = __fmul_rn(p01, p01);
+        float rt = __fsqrt_rn(__fmaf_rn(h, h, p01sq));
+        float half_tr = __fmul_rn(0.5f, __fadd_rn(p00, p11));
+        float lmax_p = __fadd_rn(half_tr, rt);
+        float ac = __fmul_rn(a, c);
+        float det = __fmul_rn(ac, ac);
+        bool whole = false;
+        float lo_x = 0.f, hi_x = 0.f, lo_y = 0.f, hi_y = 0.f;
+        if (det == 0.0f) {
+            whole = true;
+        } else {
+            float lmax_s = __fdiv_rn(lmax_p, det);
+            float rad = __fsqrt_rn(__fmul_rn(g.qmax, lmax_s));
+            rad = __fmul_rn(rad, 1.0f + 0x1p-10f);
+            const float T = (float)g.T;
+            lo_x = __fdiv_rn(__fsub_rn(mx, rad), T);
+            hi_x = __fdiv_rn(__fadd_rn(mx, rad), T);
+            lo_y = __fdiv_rn(__fsub_rn(my, rad), T);
+            hi_y = __fdiv_rn(__fadd_rn(my, rad), T);
+            if (!isfinite(rad) || !isfinite(lo_x) || !isfinite(hi_x) || !isfinite(lo_y) ||
+                !isfinite(hi_y))
+                whole = true;
+        }
+        if (whole) {
+            rect = make_int4(0, 0, im.tiles_x - 1, im.tiles_y - 1);
+        } else {
+            float fx0 = fmaxf(floorf(lo_x), 0.0f);
+            float fy0 = fmaxf(floorf(lo_y), 0.0f);
+            float fx1 = fminf(floorf(hi_x), (float)(im.tiles_x - 1));
+            float fy1 = fminf(floorf(hi_y), (float)(im.tiles_y - 1));
+            if (fx0 <= fx1 && fy0 <= fy1)
+                rect = make_int4((int)fx0, (int)fy0, (int)fx1, (int)fy1);
+        }
+    }
+    w.rect[k] = rect;
+    for (int ty = rect.y; ty <= rect.w; ++ty)
+        for (int tx = rect.x; tx <= rect.z; ++tx)
+            atomicAdd(&w.tile_cnt[im.t_off + (int64_t)ty * im.tiles_x + tx], 1);
+}
+
+// Block-wide exclusive scan of one long long per thread (1024 threads).
+__device__ long long block_exscan(long long v, long long *total) {
+    __shared__ long long warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        long long s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    long long base = wid ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(int64_t n, const int32_t *cnt,
+                                                              long long *bsum,
+                                                              const int32_t *status) {
+    if (status_bad(status)) return;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += cnt[base + i];
+    long long total;
+    block_exscan(s, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int nb, long long *bsum, int64_t n,
+                                                           int32_t *tile_off, int64_t *n_pairs,
+                                                           int64_t cap, int32_t *status) {
+    if (status_bad(status)) return;
+    // nb <= kScanChunk: each thread scans up to kScanItems consecutive sums.
+    const int base = threadIdx.x * kScanItems;
+    long long v[kScanItems], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < nb ? bsum[base + i] : 0;
+        s += v[i];
+    }
+    long long total;
+    long long run = block_exscan(s, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < nb) bsum[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) {
+        *n_pairs = total;
+        tile_off[n] = (int32_t)(total < cap ? total : cap);
+        if (total > cap) atomicCAS(status, 0, (int32_t)SMOE_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const int32_t *cnt,
+                                                            const long long *bsum,
+                                                            int32_t *tile_off, int32_t *cursor,
+                                                            int64_t cap,
+                                                            const int32_t *status) {
+    if (status_bad(status)) return;
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    long long v[kScanItems], s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = base + i < n ? cnt[base + i] : 0;
+        s += v[i];
+    }
+    long long total;
+    long long run = block_exscan(s, &total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) {
+            tile_off[base + i] = (int32_t)(run < cap ? run : cap);
+            cursor[base + i] = 0;
+        }
+        run += v[i];
+    }
+}
+
+__global__ void k_scatter(const __grid_constant__ Geo g, Bufs w) {
+    if (status_bad(w.status)) return;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= g.K_total) return;
+    const int4 rect = w.rect[k];
+    if (rect.x > rect.z) return;
+    const ImgDev &im = img_of(g, img_by_kernel(g, k));
+    for (int ty = rect.y; ty <= rect.w; ++ty)
+        for (int tx = rect.x; tx <= rect.z; ++tx) {
+            const int64_t t = im.t_off + (int64_t)ty * im.tiles_x + tx;
+            const int slot = atomicAdd(&w.cursor[t], 1);
+            w.pair_tmp[(int64_t)w.tile_off[t] + slot] = (int32_t)k;
+        }
+}
+
+__device__ int block_exscan_int(int v, int *total) {
+    __shared__ int ws[kSortThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    int base = 0, tot = 0;
+    for (int i = 0; i < kSortThreads / 32; ++i) {
+        if (i < wid) base += ws[i];
+        tot += ws[i];
+    }
+    __syncthreads();
+    *total = tot;
+    return base + x - v;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_segsort(const __grid_constant__ Geo g, Bufs w) {
+    if (status_bad(w.status)) return;
+    __shared__ uint32_t s[kBitmapWords];
+    const int64_t t = blockIdx.x;
+    const int64_t start = w.tile_off[t];
+    const int n = (int)(w.tile_off[t + 1] - start);
+    if (n <= 0) return;
+    const int tid = threadIdx.x;
+    if (n <= kSortMax) {
+        int P = 1;
+        while (P < n) P <<= 1;
+        int *v = reinterpret_cast<int *>(s);
+        for (int i = tid; i < P; i += kSortThreads)
+            v[i] = i < n ? w.pair_tmp[start + i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < P; i += kSortThreads) {
+                    const int ixj = i ^ j;
+                    if (ixj > i) {
+                        const int a = v[i], b = v[ixj];
+                        const bool up = (i & k) == 0;
+                        if ((a > b) == up) { v[i] = b; v[ixj] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = tid; i < n; i += kSortThreads) w.pair_k[start + i] = v[i];
+        return;
+    }
+    // Long list: sweep the owning image's kernel-id range with a bitmap.
+    const ImgDev &im = img_of(g, img_by_tile(g, t));
+    const int64_t win = (int64_t)kBitmapWords * 32;
+    int64_t out = start;
+    for (int64_t w0 = im.k_off; w0 < im.k_off + im.K; w0 += win) {
+        for (int i = tid; i < kBitmapWords; i += kSortThreads) s[i] = 0u;
+        __syncthreads();
+        for (int i = tid; i < n; i += kSortThreads) {
+            const int64_t d = (int64_t)w.pair_tmp[start + i] - w0;
+            if (d >= 0 && d < win) atomicOr(&s[d >> 5], 1u << (d & 31));
+        }
+        __syncthreads();
+        constexpr int per = kBitmapWords / kSortThreads;
+        int cnt = 0;
+        for (int q = 0; q < per; ++q) cnt += __popc(s[tid * per + q]);
+        int total;
+        int64_t pos = out + block_exscan_int(cnt, &total);
+        for (int q = 0; q < per; ++q) {
+            uint32_t word = s[tid * per + q];
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                w.pair_k[pos++] = (int32_t)(w0 + (int64_t)(tid * per + q) * 32 + bit);
+            }
+        }
+        out += total;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
+    const int64_t n = g.tiles_total;
+    cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * n, st);
+    if (e != cudaSuccess) return e;
+    if (g.K_total > 0) {
+        const unsigned gb = (unsigned)((g.K_total + 255) / 256);
+        k_prep_bbox<<<gb, 256, 0, st>>>(g, w);
+    }
+    const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.status);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(nb, w.bsum, n, w.tile_off, w.n_pairs, w.pair_cap,
+                                           w.status);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.tile_off, w.cursor,
+                                             w.pair_cap, w.status);
+    if (g.K_total > 0) {
+        const unsigned gb = (unsigned)((g.K_total + 255) / 256);
+        k_scatter<<<gb, 256, 0, st>>>(g, w);
+    }
+    k_segsort<<<(unsigned)n, kSortThreads, 0, st>>>(g, w);
+    return cudaGetLastError();
+}
+
+int64_t scan_blocks(int64_t n_tiles) { return (n_tiles + kScanChunk - 1) / kScanChunk; }
+
+}  // namespace smoe

@@ -1,0 +1,142 @@
+// Internal declarations shared by the CUDA translation units of libsmoe.so.
+//
+// Data layout in HBM
+//   - user parameters: FP32 SoA (mu[K][2] normalised, chol[K][3], ea[K][C],
+//     eW[K][C][2]), see include/smoe.h;
+//   - prepared record per kernel (written by the prep/bbox kernel, read by
+//     every tile kernel with one contiguous load): S floats,
+//       [0] mx  [1] my   centre in output pixels (float product mu * W)
+//       [2] a   [3] b  [4] c   L / s
+//       [5] [6] spare
+//       [7 + c*E + 0] ea_c, [7 + c*E + 1] eW_c0 / s, [7 + c*E + 2] eW_c1 / s
+//     with E = 3 for linear and 1 for constant experts, S = round_up(7+C*E, 4)
+//     (16 floats = 64 B for RGB linear experts);
+//   - backward accumulator per kernel: GS floats of raw per-kernel sums
+//     (see render.cu), GS = round_up(5 + C*E, 4);
+//   - tile lists: CSR tile_off / pair_k over the global tile index of a batch
+//     (image b's tiles start at t_off, row-major inside the image).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/smoe.h"
+
+namespace smoe {
+
+constexpr int kMaxC = 3;
+constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
+
+struct ImgDev {
+    int32_t W, H, tiles_x, tiles_y;
+    int64_t K, k_off, t_off;
+    const float *target;
+    int32_t iters;
+    float lr_mu0, lr_mu1, lr_chol, lr_ea, lr_eW;
+};
+
+struct Geo {
+    int32_t C, T, linear, S, GS;
+    float qmax, scale;
+    int32_t B;
+    int64_t K_total, tiles_total;
+    const ImgDev *table;   // device array of B entries, or nullptr (then `one`)
+    ImgDev one;
+    // user SoA parameters of all kernels of the launch (global kernel ids)
+    const float *mu, *chol, *ea, *eW;
+};
+
+struct Bufs {
+    float *rec;
+    int4 *rect;
+    int32_t *tile_cnt;
+    int32_t *cursor;
+    long long *bsum;
+    int32_t *pair_tmp;
+    float *acc;
+    int32_t *tile_off;
+    int32_t *pair_k;
+    int64_t *n_pairs;
+    int64_t pair_cap;
+    int32_t *status;
+};
+
+__host__ __device__ inline int rec_stride(int C, int linear) {
+    return (7 + C * (linear ? 3 : 1) + 3) & ~3;
+}
+__host__ __device__ inline int acc_stride(int C, int linear) {
+    return (5 + C * (linear ? 3 : 1) + 3) & ~3;
+}
+
+__device__ __forceinline__ const ImgDev &img_of(const Geo &g, int b) {
+    return g.table ? g.table[b] : g.one;
+}
+
+// Image that owns global kernel k / global tile t (binary search, B small).
+__device__ __forceinline__ int img_by_kernel(const Geo &g, int64_t k) {
+    if (!g.table) return 0;
+    int lo = 0, hi = g.B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.table[mid].k_off <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int img_by_tile(const Geo &g, int64_t t) {
+    if (!g.table) return 0;
+    int lo = 0, hi = g.B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.table[mid].t_off <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Hardware base-2 exponential (MUFU.EX2), flush-to-zero.  Arguments on the
+// hot path lie in [-0.72 q_max, 0], far from the subnormal range.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Truncation predicate pieces, one IEEE rounding per step (no contraction):
+//   per row:   dy = y0 - my, t = b*dy, z1 = c*dy, u = z1*z1
+//   per pixel: dx = x0 - mx, z0 = fma(a, dx, t), q = fma(z0, z0, u)
+__device__ __forceinline__ float q_of(float a, float dx, float t, float u, float &z0) {
+    z0 = __fmaf_rn(a, dx, t);
+    return __fmaf_rn(z0, z0, u);
+}
+
+// Gate numerator for a pair: exp(-q/2) if q <= q_max else 0.
+__device__ __forceinline__ float gate_e(float q, float qmax) {
+    float e = ex2(__fmul_rn(q, kNegHalfLog2e));
+    return q <= qmax ? e : 0.0f;
+}
+
+__device__ __forceinline__ bool status_bad(const int32_t *status) {
+    return status && *(volatile const int32_t *)status != 0;
+}
+
+// --------------------------------------------------------------------------
+// launchers (host side, no synchronisation)
+// --------------------------------------------------------------------------
+cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st);
+cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
+                          cudaStream_t st);
+cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const float *inv_d,
+                              const float *gy, const float *target, const smoe_params &grad,
+                              cudaStream_t st);
+cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,
+                             const int32_t *step, cudaStream_t st);
+cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
+                            const smoe_params &v, int C, const float lr[4], float b1, float b2,
+                            float eps, int32_t step, cudaStream_t st);
+cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
+                            float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
+                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, float b1,
+                            float b2, float eps, int32_t *step, uint32_t *done,
+                            cudaStream_t st);
+cudaError_t launch_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out,
+                            cudaStream_t st);
+
+}  // namespace smoe

@@ -1,0 +1,163 @@
+"""Fit driver over smoe_fit: one image or a ragged batch of images, each
+iteration = binning, one fused forward/MSE/backward launch over the ragged
+tile table of all images, one fused finalize + Adam launch.  Iterations can
+be captured in a CUDA graph and replayed; the pair buffer grows (and the run
+continues) if an iteration overflows it."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SmoeError, check
+from .api import RasterDesc, Rasterizer, SMoEParams, _ptr, _stream, smoe_get_status
+
+
+class FitBatch:
+    """B images fitted together.
+
+    targets: list of (C,H,W) float32 CUDA tensors; params: list of SMoEParams
+    (initial values, copied into one batch SoA); iters: per-image run length
+    (int or list); lr = (mu0, mu1, chol, ea, eW)."""
+
+    def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
+                 qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
+                 device="cuda"):
+        assert len(targets) == len(params) and len(targets) > 0
+        self.B = len(targets)
+        self.device = device
+        self.C = params[0].C
+        self.linear = params[0].linear
+        self.tile, self.qmax = tile, qmax
+        self.b1, self.b2, self.eps = b1, b2, eps
+        self.targets = [t.contiguous() for t in targets]
+        self.iters = [iters] * self.B if np.isscalar(iters) else list(iters)
+        self.lr = [lr] * self.B if np.isscalar(lr[0]) else list(lr)
+        self.Ks = [p.K for p in params]
+        self.k_off = np.concatenate([[0], np.cumsum(self.Ks)]).astype(np.int64)
+        cat = lambda xs: torch.cat([x for x in xs], 0).contiguous()
+        self.p = SMoEParams(cat([p.mu for p in params]), cat([p.chol for p in params]),
+                            cat([p.ea for p in params]),
+                            cat([p.eW for p in params]) if self.linear else None)
+        self.m = self.p.zeros_like()
+        self.v = self.p.zeros_like()
+        self.step = torch.zeros(self.B, dtype=torch.int32, device=device)
+        self.hist = int(hist if hist is not None else max(self.iters))
+        self.loss = torch.zeros(self.B, max(self.hist, 1), dtype=torch.float64, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.graph = None
+        # Pair capacity: bin each image once with its initial parameters.
+        total = 0
+        for b in range(self.B):
+            t = self.targets[b]
+            desc = RasterDesc(t.shape[2], t.shape[1], self.C, tile, self.linear, qmax, 1.0)
+            r = Rasterizer(desc, self.Ks[b]).bin(self.params_of(b))
+            total += int(r.n_pairs.item())
+        self.pair_cap = int(total * pair_slack) + 4096
+        self._setup(reset=True)
+
+    # -- C structs
+    def _structs(self):
+        imgs = (_lib.FitImage * self.B)()
+        for b in range(self.B):
+            t = self.targets[b]
+            lr = self.lr[b]
+            imgs[b] = _lib.FitImage(t.shape[2], t.shape[1], self.Ks[b], int(self.k_off[b]),
+                                    _ptr(t), int(self.iters[b]), lr[0], lr[1], lr[2], lr[3],
+                                    lr[4])
+        batch = _lib.FitBatch(self.B, self.C, self.tile, int(self.linear), self.qmax, self.b1,
+                              self.b2, self.eps, self.p.c(), self.m.c(), self.v.c(),
+                              _ptr(self.step), _ptr(self.loss), self.hist)
+        return batch, imgs
+
+    def _setup(self, reset):
+        lib = _lib.load()
+        self._batch, self._imgs = self._structs()
+        n = ctypes.c_size_t(0)
+        check(lib.smoe_fit_workspace_size(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                          ctypes.byref(n)), "smoe_fit_workspace_size")
+        raw = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        self.ws = raw[off:off + n.value]
+        if not reset:
+            self.status.zero_()
+        check(lib.smoe_fit_init(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                _ptr(self.ws), self.ws.numel(), int(reset), _ptr(self.status),
+                                _stream(None)), "smoe_fit_init")
+        self.graph = None
+
+    def params_of(self, b):
+        s, e = int(self.k_off[b]), int(self.k_off[b + 1])
+        return SMoEParams(self.p.mu[s:e], self.p.chol[s:e], self.p.ea[s:e],
+                          None if self.eW is None else self.eW[s:e])
+
+    @property
+    def eW(self):
+        return self.p.eW
+
+    def launch(self, n_iters=1, stream=None):
+        """Enqueue n_iters iterations (no host synchronisation)."""
+        check(_lib.load().smoe_fit(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                   _ptr(self.ws), self.ws.numel(), n_iters, _ptr(self.status),
+                                   _stream(stream)), "smoe_fit")
+
+    def phase(self, phase, stream=None):
+        """Enqueue one phase (0 bin, 1 fused tiles, 2 Adam) of one iteration."""
+        check(_lib.load().smoe_fit_phase(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                         _ptr(self.ws), self.ws.numel(), phase,
+                                         _ptr(self.status), _stream(stream)), "smoe_fit_phase")
+
+    def capture(self, n_iters=1):
+        """Capture n_iters iterations into a CUDA graph."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.launch(0)          # warm the library's launch path outside capture
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.launch(n_iters)
+        self.graph, self.graph_iters = g, n_iters
+        return g
+
+    def status_code(self):
+        return smoe_get_status(self.status)
+
+    def run(self, n_iters, graph_iters=None, check_every=None):
+        """Run n_iters iterations; with graph_iters, as replays of a captured
+        graph of that many iterations.  The status is checked after every
+        `check_every` iterations (default: at the end); a pair-buffer overflow
+        grows the buffer and resumes from where the run stopped."""
+        done = 0
+        check_every = check_every or n_iters
+        while done < n_iters:
+            chunk = min(check_every, n_iters - done)
+            before = self.step.clone()
+            if graph_iters:
+                if self.graph is None or self.graph_iters != graph_iters:
+                    self.capture(graph_iters)
+                reps = chunk // graph_iters
+                for _ in range(reps):
+                    self.graph.replay()
+                rest = chunk - reps * graph_iters
+                if rest:
+                    self.launch(rest)
+            else:
+                self.launch(chunk)
+            st = self.status_code()
+            if st == _lib.SMOE_ERR_CAPACITY:
+                # Grow the pair buffer and continue where the run stopped.
+                self.pair_cap = int(self.pair_cap * 1.5) + 4096
+                self._setup(reset=False)
+                progressed = int((self.step - before).max().item())
+                done += progressed
+                continue
+            if st != _lib.SMOE_OK:
+                raise SmoeError(st, "smoe_fit")
+            done += chunk
+        return self
+
+    def losses(self):
+        return self.loss.cpu().numpy()

@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar (element by element on the same seeded inputs):
+  - tile lists: bit-exact;
+  - render: |y - y_ref| <= 1e-5 * max(|y_ref|, sum_k w_k |m_k|) per pixel and
+    channel (FP32 against the FP64 oracle), 1/D within 1e-5 relative;
+  - gradients: per element |g - g_ref| <= 1e-4 * max(|g_ref|, 1e-3 * max|g_ref|
+    of the group);
+  - Adam: within FP32 rounding of the FP64 update.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as om  # noqa: E402
+from paper_2510_05814_gb300 import api, synth  # noqa: E402
+from paper_2510_05814_gb300.fit import FitBatch  # noqa: E402
+
+RTOL_Y = 1e-5
+RTOL_G = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_05814_gb300 import build
+    build.build()
+    om.build()
+
+
+def rand_case(seed, W, H, C, K, linear, sig=(1.5, 6.0), span=(-0.05, 1.05)):
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(*span, (K, 2))
+    chol = np.zeros((K, 3))
+    for k in range(K):
+        s = rng.uniform(*sig, 2)
+        th = rng.uniform(0, np.pi)
+        R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        L = np.linalg.cholesky(np.linalg.inv(R @ np.diag(s ** 2) @ R.T))
+        chol[k] = (L[0, 0], L[1, 0], L[1, 1])
+    ea = rng.uniform(0, 1, (K, C))
+    eW = rng.normal(0, 0.05, (K, C, 2)) if linear else None
+    return synth.Params(mu.astype(np.float32), chol.astype(np.float32), ea.astype(np.float32),
+                        None if eW is None else eW.astype(np.float32))
+
+
+def degenerate_case(W, H, C, linear):
+    mu = [[0.5, 0.5], [0.5, 0.5], [0.5, 0.5], [0.3, 0.7], [1.4, 0.5], [-0.2, -0.2], [0.0, 0.0],
+          [1.0, 1.0], [0.5, 0.5], [np.nan, 0.5], [0.25, 0.25], [0.6, 0.4]]
+    chol = [[0.0, 0.3, 0.3], [0.3, 0.1, 0.0], [1e-30, 0.0, 1e-30], [5.0, 0.0, 5.0],
+            [0.2, 0.0, 0.2], [0.05, 0.0, 0.05], [0.5, 0.0, 0.5], [0.5, 0.0, 0.5],
+            [np.inf, 0.0, 0.3], [0.3, 0.0, 0.3], [-0.3, 0.2, -0.4], [0.25, -0.9, 0.05]]
+    K = len(mu)
+    rng = np.random.default_rng(99)
+    return synth.Params(np.array(mu, np.float32), np.array(chol, np.float32),
+                        rng.uniform(0, 1, (K, C)).astype(np.float32),
+                        rng.normal(0, 0.05, (K, C, 2)).astype(np.float32) if linear else None)
+
+
+def oracle_model(p, W, H, C, tile, qmax=9.0, scale=1.0):
+    return om.Model(W, H, C, p.mu, p.chol, p.ea, p.eW, tile=tile, qmax=qmax, scale=scale)
+
+
+# (seed, W, H, C, K, linear, tile, scale, kind)
+CASES = [
+    (1, 64, 64, 1, 40, False, 16, 1.0, "rand"),
+    (2, 53, 47, 3, 60, True, 8, 1.0, "rand"),       # ragged edges, T=8
+    (3, 77, 45, 3, 50, True, 16, 1.0, "rand"),
+    (4, 70, 66, 1, 45, True, 32, 1.0, "rand"),       # T=32, ragged
+    (5, 96, 64, 3, 30, False, 32, 1.0, "rand"),
+    (6, 41, 39, 3, 12, True, 8, 1.0, "degenerate"),
+    (7, 41, 39, 1, 12, False, 16, 1.0, "degenerate"),
+    (8, 60, 50, 3, 35, True, 16, 1.5, "rand"),        # super-resolution scale
+    (9, 80, 80, 3, 30, True, 8, 2.0, "rand"),
+    (10, 1, 1, 3, 5, True, 8, 1.0, "rand"),          # 1x1 image
+    (11, 33, 17, 1, 1, True, 16, 1.0, "rand"),        # one kernel
+]
+
+
+def case_data(case):
+    seed, W, H, C, K, linear, tile, scale, kind = case
+    if kind == "degenerate":
+        p = degenerate_case(W, H, C, linear)
+    else:
+        p = rand_case(seed, int(round(W / scale)), int(round(H / scale)), C, K, linear)
+    return p, W, H, C, tile, scale
+
+
+def gpu_raster(p, W, H, C, tile, scale, qmax=9.0, pair_cap=None):
+    params = api.SMoEParams.from_numpy(p)
+    desc = api.RasterDesc(W, H, C, tile, p.eW is not None, qmax, scale)
+    r = api.Rasterizer(desc, params.K, pair_cap=pair_cap).bin(params)
+    return params, r
+
+
+def check_y(y, ref, scale, what=""):
+    tol = RTOL_Y * np.maximum(np.abs(ref), scale)
+    err = np.abs(y - ref)
+    bad = err > tol
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} over tolerance, max err {err.max()}"
+
+
+def check_grad(g, ref, what=""):
+    ref = np.asarray(ref, np.float64)
+    floor = 1e-3 * np.abs(ref).max() if ref.size else 0.0
+    den = np.maximum(np.abs(ref), floor)
+    rel = np.abs(np.asarray(g, np.float64) - ref) / np.where(den > 0, den, 1.0)
+    assert rel.max() <= RTOL_G, f"{what}: max rel err {rel.max():.3g}"
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"c{c[0]}" for c in CASES])
+def test_bin_bitexact(case):
+    p, W, H, C, tile, scale = case_data(case)
+    _, r = gpu_raster(p, W, H, C, tile, scale)
+    off, pk = r.lists()
+    ref_off, ref_pk = om.bin_tiles(oracle_model(p, W, H, C, tile, scale=scale))
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    assert int(r.n_pairs.item()) == int(ref_off[-1])
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"c{c[0]}" for c in CASES])
+def test_render_parity(case):
+    p, W, H, C, tile, scale = case_data(case)
+    _, r = gpu_raster(p, W, H, C, tile, scale)
+    y, invd = r.render()
+    ref, ref_invd, absm = om.render(oracle_model(p, W, H, C, tile, scale=scale), with_scale=True)
+    check_y(y.cpu().numpy(), ref, absm, "y")
+    inv = invd.cpu().numpy()
+    assert np.all(np.abs(inv - ref_invd) <= RTOL_Y * ref_invd)
+
+
+@pytest.mark.parametrize("case", CASES, ids=[f"c{c[0]}" for c in CASES])
+def test_backward_parity(case):
+    p, W, H, C, tile, scale = case_data(case)
+    params, r = gpu_raster(p, W, H, C, tile, scale)
+    y, invd = r.render()
+    rng = np.random.default_rng(case[0] + 1000)
+    gy = rng.normal(0, 1, (C, H, W))
+    g = r.backward(params, y, invd, gy=torch.tensor(gy, dtype=torch.float32, device="cuda"))
+    gy32 = gy.astype(np.float32).astype(np.float64)
+    ref = om.backward(oracle_model(p, W, H, C, tile, scale=scale), gy=gy32)
+    for name, a, b in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref):
+        if b is not None:
+            check_grad(a, b, name)
+
+
+def test_fused_mse_backward_parity():
+    p = rand_case(21, 72, 60, 3, 50, True)
+    params, r = gpu_raster(p, 72, 60, 3, 16, 1.0)
+    y, invd = r.render()
+    t = synth.polygon_image(72, 60, 3, 5, 21)
+    g = r.backward(params, y, invd, target=torch.tensor(t, device="cuda"))
+    ref = om.backward(oracle_model(p, 72, 60, 3, 16), target=t)
+    for name, a, b in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref):
+        check_grad(a, b, name)
+
+
+def test_long_lists_use_bitmap_path():
+    """3000 wide kernels on a 40x40 image: every tile list (3000 > 2048) goes
+    through the bitmap sweep; lists, render and gradients still match."""
+    p = rand_case(31, 40, 40, 1, 3000, False, sig=(25.0, 40.0), span=(0.2, 0.8))
+    params, r = gpu_raster(p, 40, 40, 1, 16, 1.0)
+    off, pk = r.lists()
+    m = oracle_model(p, 40, 40, 1, 16)
+    ref_off, ref_pk = om.bin_tiles(m)
+    assert np.diff(ref_off).min() > 2048
+    np.testing.assert_array_equal(pk, ref_pk)
+    y, invd = r.render()
+    ref, _, absm = om.render(m, with_scale=True)
+    check_y(y.cpu().numpy(), ref, absm, "y")
+
+
+def test_empty_model_and_offimage_kernels():
+    p = synth.Params(np.array([[3.0, 3.0], [-2.0, 0.5]], np.float32),
+                     np.array([[0.3, 0.0, 0.3], [0.3, 0.0, 0.3]], np.float32),
+                     np.ones((2, 3), np.float32), np.zeros((2, 3, 2), np.float32))
+    params, r = gpu_raster(p, 32, 32, 3, 16, 1.0)
+    assert int(r.n_pairs.item()) == 0
+    y, invd = r.render()
+    assert torch.count_nonzero(y).item() == 0 and torch.count_nonzero(invd).item() == 0
+    g = r.backward(params, y, invd, gy=torch.ones_like(y))
+    assert all(torch.count_nonzero(t).item() == 0 for t in g.tensors())
+
+
+def test_capacity_overflow_sets_status_and_grows():
+    p = rand_case(41, 64, 64, 3, 80, True)
+    params = api.SMoEParams.from_numpy(p)
+    desc = api.RasterDesc(64, 64, 3, 16, True)
+    r = api.Rasterizer(desc, params.K, pair_cap=4)
+    r.status.zero_()
+    api.smoe_bin(desc, params, r.ws, r.tile_off, r.pair_k, r.n_pairs, r.status)
+    assert api.smoe_get_status(r.status) == 2            # SMOE_ERR_CAPACITY
+    need = int(r.n_pairs.item())
+    assert need > 4
+    r.bin(params)                                          # grows and re-bins
+    assert r.pair_cap >= need
+    ref_off, ref_pk = om.bin_tiles(oracle_model(p, 64, 64, 3, 16))
+    np.testing.assert_array_equal(r.lists()[1], ref_pk)
+
+
+def test_deterministic_lists_and_render():
+    p = rand_case(51, 100, 90, 3, 200, True)
+    _, r1 = gpu_raster(p, 100, 90, 3, 16, 1.0)
+    _, r2 = gpu_raster(p, 100, 90, 3, 16, 1.0)
+    y1, i1 = r1.render()
+    y2, i2 = r2.render()
+    assert torch.equal(r1.pair_k[: r1.pair_cap], r2.pair_k[: r2.pair_cap]) or \
+        np.array_equal(r1.lists()[1], r2.lists()[1])
+    assert torch.equal(y1, y2) and torch.equal(i1, i2)
+
+
+def test_adam_parity():
+    rng = np.random.default_rng(61)
+    K, C = 500, 3
+    mk = lambda: api.SMoEParams.from_numpy(synth.Params(
+        rng.normal(0, 1, (K, 2)).astype(np.float32), rng.normal(0, 1, (K, 3)).astype(np.float32),
+        rng.normal(0, 1, (K, C)).astype(np.float32), rng.normal(0, 1, (K, C, 2)).astype(np.float32)))
+    p, m = mk(), mk()
+    v = api.SMoEParams(*(t.abs() for t in mk().tensors()))
+    lr = (1e-2, 1e-3, 2e-3, 5e-4)
+    ref = [[t.cpu().numpy().astype(np.float64).ravel().copy() for t in x.tensors()] for x in (p, m, v)]
+    for step in (1, 2, 3):
+        g = mk()
+        gref = [t.cpu().numpy().astype(np.float64).ravel() for t in g.tensors()]
+        api.smoe_adam_step(p, g, m, v, lr, 0.9, 0.999, 1e-8, step)
+        for gi in range(4):
+            om.adam(ref[0][gi], gref[gi].copy(), ref[1][gi], ref[2][gi], lr[gi], 0.9, 0.999, 1e-8, step)
+        assert all(torch.count_nonzero(t).item() == 0 for t in g.tensors())   # grads zeroed
+        for gi, t in enumerate(p.tensors()):
+            got = t.cpu().numpy().astype(np.float64).ravel()
+            assert np.all(np.abs(got - ref[0][gi]) <= 4e-7 * np.abs(ref[0][gi]) + 1e-5 * lr[gi])
+            # continue from the GPU state so rounding does not accumulate
+            ref[0][gi] = got.copy()
+            ref[1][gi] = m.tensors()[gi].cpu().numpy().astype(np.float64).ravel().copy()
+            ref[2][gi] = v.tensors()[gi].cpu().numpy().astype(np.float64).ravel().copy()
+
+
+def test_fit_matches_oracle_trajectory():
+    """smoe_fit (B = 1) follows the oracle's FP64 fit: per-iteration MSE
+    within 1e-4 relative over 8 iterations of the 128x128 grey workload's
+    48x48 crop (constant experts, lr 1e-2)."""
+    wl = synth.plain_gray_128()
+    t = wl.target[:, :48, :48].copy()
+    p = synth.init_params(t, 36, 8.0 * 48 / 128, False, 1)
+    m = om.Model(48, 48, 1, p.mu.copy(), p.chol.copy(), p.ea.copy(), tile=16)
+    ref_loss = om.fit(m, t, 8, lr=(1e-2,) * 5)
+    fb = FitBatch([torch.tensor(t, device="cuda")], [api.SMoEParams.from_numpy(p)], 8,
+                  lr=(1e-2,) * 5, tile=16)
+    fb.run(8)
+    got = fb.losses()[0]
+    np.testing.assert_allclose(got, ref_loss, rtol=1e-4)
+    np.testing.assert_allclose(fb.p.mu.cpu().numpy(), m.mu, rtol=0, atol=2e-5)
+
+
+def test_batched_fit_equals_single_image_fits():
+    """A ragged batch of three images gives each image the same result as
+    fitting it alone (FP32 atomics: within 1e-5)."""
+    sizes = [(40, 30), (64, 48), (23, 37)]
+    ts, ps = [], []
+    for i, (W, H) in enumerate(sizes):
+        t = synth.polygon_image(W, H, 3, 4, 70 + i)
+        ts.append(torch.tensor(t, device="cuda"))
+        ps.append(api.SMoEParams.from_numpy(synth.init_params(t, (W * H) // 16, 3.0, True, 70 + i)))
+    lr = (1e-2, 1e-3, 1e-2, 1e-2, 1e-2)
+    fb = FitBatch(ts, [p.clone() for p in ps], 6, lr=lr, tile=8).run(6)
+    for b in range(3):
+        one = FitBatch([ts[b]], [ps[b].clone()], 6, lr=lr, tile=8).run(6)
+        a, o = fb.params_of(b), one.params_of(0)
+        for x, y in zip(a.tensors(), o.tensors()):
+            assert torch.allclose(x, y, rtol=1e-5, atol=1e-6)
+        np.testing.assert_allclose(fb.losses()[b], one.losses()[0], rtol=1e-5)
+
+
+def test_graph_replay_equals_eager():
+    t = synth.polygon_image(64, 64, 3, 6, 81)
+    p = api.SMoEParams.from_numpy(synth.init_params(t, 256, 3.0, True, 81))
+    tt = torch.tensor(t, device="cuda")
+    a = FitBatch([tt], [p.clone()], 12, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2)).run(12)
+    b = FitBatch([tt], [p.clone()], 12, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2)).run(12, graph_iters=4)
+    np.testing.assert_allclose(a.losses(), b.losses(), rtol=1e-5)
+    assert int(b.step.item()) == 12
