@@ -39,7 +39,7 @@ UNIT = "Gpix·kernel evals/s"
 WORKLOAD = ("rgb2048_K262144_linear_aniso: 2048x2048 RGB fp32, 40 ramp polygons + Perlin "
             "texture 0.1, K=262144 anisotropic kernels (area sigma 5 px, aspect 1-3), linear "
             "experts, 16x16 tiles, q_max 9, Adam at the paper's rates")
-MUFU_PER_CLK_PER_SM = 16          # ex2 results per clock per SM (sm_80 .. sm_10x)
+MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM, measured on GB300 (sm_103)
 # DRAM bytes per launch of the fused tile kernel from one ncu capture (see
 # profiles/); valid only while render.cu is the file that was profiled.
 TRAFFIC = {"render_cu_sha256": None, "bytes_per_launch": None}
@@ -183,7 +183,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-crop", type=int, default=512)

@@ -142,13 +142,14 @@ SMOE_API smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params 
                                  const smoe_params *grad, const int32_t *status,
                                  void *stream);
 
-/* Adam (Sec. VI-B), torch semantics, FP32, one fused launch over the four
- * parameter groups; zeroes g.  lr = {mu, chol, ea, eW}; step >= 1 is the
+/* Adam (Sec. VI-B), torch semantics, FP32 state, one fused launch over the
+ * four parameter groups; zeroes g.  1 - b1, 1 - b2 and the bias corrections
+ * are formed in FP64 and rounded once.  lr = {mu, chol, ea, eW}; step >= 1 is the
  * 1-based step used for the bias corrections.  C is the channel count
  * (sizes of ea / eW).  eW pointers must all be NULL or all non-NULL. */
 SMOE_API smoe_status smoe_adam_step(const smoe_params *p, const smoe_params *g, const smoe_params *m,
-                           const smoe_params *v, int32_t C, const float lr[4], float b1,
-                           float b2, float eps, int32_t step, void *stream);
+                           const smoe_params *v, int32_t C, const float lr[4], double b1,
+                           double b2, double eps, int32_t step, void *stream);
 
 /* Sum of squared differences over n floats, FP64 accumulation, ADDED to
  * *out (device); with clamp != 0, y is clamped to [0, 1] first (the PSNR
@@ -175,7 +176,7 @@ typedef struct {
     int32_t B;              /* images */
     int32_t C, tile, expert;
     float qmax;
-    float b1, b2, eps;      /* Adam */
+    double b1, b2, eps;     /* Adam (1 - b and the bias corrections are formed in FP64) */
     smoe_params p, m, v;    /* batch SoA (device): K_total kernels, image b at k_off */
     int32_t *step;          /* device, B: iterations done per image (caller-owned) */
     double *loss;           /* device, B x hist: MSE per image and iteration, or NULL */

@@ -63,7 +63,7 @@ def _load():
         lib.om_bin.restype = I64
         lib.om_render.argtypes = [MP, I64, P, P, P, P]
         lib.om_render.restype = None
-        lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P]
+        lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P, P, P, P, P]
         lib.om_backward.restype = None
         lib.om_adam.argtypes = [I64, P, P, P, P, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int32]
@@ -179,26 +179,29 @@ def render(m: Model, pixels=None, with_scale=False):
     return (y, invd, absm) if with_scale else (y, invd)
 
 
-def backward(m: Model, gy=None, target=None, kernels=None):
+def backward(m: Model, gy=None, target=None, kernels=None, with_scale=False):
     """FP64 gradient of the loss w.r.t. (mu, chol, ea, eW) in API units.
 
     gy: upstream dL/dy (C,H,W) float64, or target (C,H,W) for the fused MSE
-    loss sum((y-t)^2)/(C H W).  kernels: optional list of kernel ids."""
+    loss sum((y-t)^2)/(C H W).  kernels: optional list of kernel ids.
+    with_scale=True also returns, per element, the sum of the magnitudes of
+    the terms that make up the gradient (the scale of FP cancellation)."""
     lib = _load()
     c = m._c()
     sel = None if kernels is None else np.ascontiguousarray(kernels, dtype=np.int64)
     n = m.K if sel is None else len(sel)
-    g_mu = np.zeros((n, 2), np.float64)
-    g_chol = np.zeros((n, 3), np.float64)
-    g_ea = np.zeros((n, m.C), np.float64)
-    g_eW = np.zeros((n, m.C, 2), np.float64) if m.linear else None
+
+    def alloc():
+        return [np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, m.C)),
+                np.zeros((n, m.C, 2)) if m.linear else None]
+    g, sc = alloc(), (alloc() if with_scale else [None] * 4)
     gy_ = None if gy is None else np.ascontiguousarray(gy, dtype=np.float64)
     t_ = None if target is None else np.ascontiguousarray(target, dtype=np.float32)
     if gy_ is None and t_ is None:
         raise ValueError("need gy or target")
     lib.om_backward(ctypes.byref(c), _ptr(gy_), _ptr(t_), 0 if sel is None else n, _ptr(sel),
-                    _ptr(g_mu), _ptr(g_chol), _ptr(g_ea), _ptr(g_eW))
-    return g_mu, g_chol, g_ea, g_eW
+                    *[_ptr(x) for x in g], *[_ptr(x) for x in sc])
+    return (tuple(g), tuple(sc)) if with_scale else tuple(g)
 
 
 def adam(p, g, m_, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):

@@ -275,7 +275,8 @@ void om_render(const om_model *m, int64_t n_px, const int64_t *px, double *y,
  * listed kernels, outputs indexed by position in ksel. */
 void om_backward(const om_model *m, const double *gy, const float *target,
                  int64_t n_sel, const int64_t *ksel, double *g_mu,
-                 double *g_chol, double *g_ea, double *g_eW)
+                 double *g_chol, double *g_ea, double *g_eW, double *s_mu,
+                 double *s_chol, double *s_ea, double *s_eW)
 {
     const int64_t HW = (int64_t)m->W * m->H;
     const int C = m->C;
@@ -315,6 +316,10 @@ void om_backward(const om_model *m, const double *gy, const float *target,
         kernel_px(m, k, &mx, &my, &a, &b, &c);
         double ga = 0, gb = 0, gc = 0, gmx = 0, gmy = 0;
         double gea[3] = {0, 0, 0}, gw[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        /* the same sums with every factor replaced by its magnitude: the
+         * size of the terms that cancel (optional outputs s_*) */
+        double sa = 0, sb = 0, sc = 0, smx = 0, smy = 0;
+        double sea[3] = {0, 0, 0}, sw[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         double w[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         for (int ch = 0; ch < C && m->linear; ++ch) {
             for (int d2 = 0; d2 < 2; ++d2) {
@@ -333,6 +338,15 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             for (int ch = 0; ch < C; ++ch)
                 r += G[ch * HW + p] * (pr.mexp[ch] - Y[ch * HW + p]);
             double sv = g * r;
+            double sabs = 0.0;
+            for (int ch = 0; ch < C; ++ch)
+                sabs += fabs(G[ch * HW + p]) * (fabs(pr.mexp[ch]) + fabs(Y[ch * HW + p]));
+            sabs *= g;
+            sa += sabs * fabs(pr.z0 * pr.dx);
+            sb += sabs * fabs(pr.z0 * pr.dy);
+            sc += sabs * fabs(pr.z1 * pr.dy);
+            smx += sabs * fabs(pr.z0 * (double)a);
+            smy += sabs * (fabs(pr.z0 * (double)b) + fabs(pr.z1 * (double)c));
             ga += -sv * pr.z0 * pr.dx;
             gb += -sv * pr.z0 * pr.dy;
             gc += -sv * pr.z1 * pr.dy;
@@ -341,11 +355,16 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             for (int ch = 0; ch < C; ++ch) {
                 double gG = g * G[ch * HW + p];
                 gea[ch] += gG;
+                sea[ch] += fabs(gG);
                 if (m->linear) {
                     gw[ch][0] += gG * pr.dx;
                     gw[ch][1] += gG * pr.dy;
                     gmx -= gG * w[ch][0];
                     gmy -= gG * w[ch][1];
+                    sw[ch][0] += fabs(gG * pr.dx);
+                    sw[ch][1] += fabs(gG * pr.dy);
+                    smx += fabs(gG * w[ch][0]);
+                    smy += fabs(gG * w[ch][1]);
                 }
             }
         }
@@ -360,6 +379,20 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             if (m->linear && g_eW) {
                 g_eW[(s * C + ch) * 2] = gw[ch][0] * inv_s;
                 g_eW[(s * C + ch) * 2 + 1] = gw[ch][1] * inv_s;
+            }
+        }
+        if (s_mu) {
+            s_mu[2 * s] = smx * (double)m->W;
+            s_mu[2 * s + 1] = smy * (double)m->H;
+            s_chol[3 * s] = sa * inv_s;
+            s_chol[3 * s + 1] = sb * inv_s;
+            s_chol[3 * s + 2] = sc * inv_s;
+            for (int ch = 0; ch < C; ++ch) {
+                s_ea[s * C + ch] = sea[ch];
+                if (m->linear && s_eW) {
+                    s_eW[(s * C + ch) * 2] = sw[ch][0] * inv_s;
+                    s_eW[(s * C + ch) * 2 + 1] = sw[ch][1] * inv_s;
+                }
             }
         }
     }
@@ -427,7 +460,7 @@ void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[5],
             loss[it] = se / (double)(HW * C);
         }
         om_backward(m, NULL, target, 0, NULL, G[0], G[1], G[2],
-                    m->linear ? G[3] : NULL);
+                    m->linear ? G[3] : NULL, NULL, NULL, NULL, NULL);
         double lrs[4] = {om_lr_mu(lr[0], lr[1], it, n_it), lr[2], lr[3], lr[4]};
         for (int gi = 0; gi < 4; ++gi)
             if (n_g[gi] > 0)

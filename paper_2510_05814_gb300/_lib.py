@@ -44,8 +44,8 @@ class FitImage(ctypes.Structure):
 
 class FitBatch(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("C", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("expert", ctypes.c_int32), ("qmax", ctypes.c_float), ("b1", ctypes.c_float),
-                ("b2", ctypes.c_float), ("eps", ctypes.c_float), ("p", Params),
+                ("expert", ctypes.c_int32), ("qmax", ctypes.c_float), ("b1", ctypes.c_double),
+                ("b2", ctypes.c_double), ("eps", ctypes.c_double), ("p", Params),
                 ("m", Params), ("v", Params), ("step", ctypes.c_void_p),
                 ("loss", ctypes.c_void_p), ("hist", ctypes.c_int32)]
 
@@ -72,7 +72,8 @@ def load():
         "smoe_bin": (I32, [D, PP, P, ctypes.c_size_t, P, P, I64, P, P, P]),
         "smoe_render": (I32, [D, I64, P, ctypes.c_size_t, P, P, P, P, P, P]),
         "smoe_render_backward": (I32, [D, PP, P, ctypes.c_size_t, P, P, P, P, P, P, PP, P, P]),
-        "smoe_adam_step": (I32, [PP, PP, PP, PP, I32, ctypes.POINTER(F32), F32, F32, F32, I32, P]),
+        "smoe_adam_step": (I32, [PP, PP, PP, PP, I32, ctypes.POINTER(F32), ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, I32, P]),
         "smoe_sq_error": (I32, [P, P, I64, I32, P, P]),
         "smoe_fit_workspace_size": (I32, [FB, FI, I64, SZ]),
         "smoe_fit_init": (I32, [FB, FI, I64, P, ctypes.c_size_t, I32, P, P]),

@@ -136,8 +136,8 @@ def smoe_adam_step(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1, stream=No
     lr4 = (ctypes.c_float * 4)(*[float(x) for x in lr])
     pc, gc, mc, vc = p.c(), g.c(), m.c(), v.c()
     check(_lib.load().smoe_adam_step(ctypes.byref(pc), ctypes.byref(gc), ctypes.byref(mc),
-                                     ctypes.byref(vc), p.C, lr4, b1, b2, eps, step,
-                                     _stream(stream)), "smoe_adam_step")
+                                     ctypes.byref(vc), p.C, lr4, float(b1), float(b2),
+                                     float(eps), step, _stream(stream)), "smoe_adam_step")
 
 
 def smoe_sq_error(y, target, out, clamp=True, stream=None):

@@ -10,23 +10,27 @@ namespace smoe {
 
 namespace {
 
+struct Betas {
+    float b2, omb1, omb2, eps;   // b2, 1 - b1, 1 - b2 (rounded once from FP64), eps
+};
+
 struct AdamK {
-    float b1, b2, eps;
+    Betas be;
     float step_size;       // lr / (1 - b1^t)
     float inv_sqrt_bc2;    // 1 / sqrt(1 - b2^t)
 };
 
 __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, const AdamK &k) {
-    m = fmaf(1.0f - k.b1, g - m, m);
-    v = fmaf(k.b2, v, (1.0f - k.b2) * g * g);
-    const float denom = sqrtf(v) * k.inv_sqrt_bc2 + k.eps;
+    m = fmaf(k.be.omb1, g - m, m);
+    v = fmaf(k.be.b2, v, k.be.omb2 * g * g);
+    const float denom = sqrtf(v) * k.inv_sqrt_bc2 + k.be.eps;
     p -= k.step_size * (m / denom);
 }
 
 // One launch over the four groups of a SoA parameter set; zeroes g.
 __global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_params gr,
                            smoe_params m, smoe_params v, float lr0, float lr1, float lr2,
-                           float lr3, float b1, float b2, float eps, float bc1, float isb2) {
+                           float lr3, Betas be, float bc1, float isb2) {
     const int64_t n_mu = 2 * K, n_ch = 3 * K, n_ea = (int64_t)C * K;
     const int64_t n_w = has_w ? 2 * (int64_t)C * K : 0;
     const int64_t total = n_mu + n_ch + n_ea + n_w;
@@ -39,7 +43,7 @@ __global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_para
         else if ((x -= n_mu) < n_ch) { pp = p.chol; gg = gr.chol; mm = m.chol; vv = v.chol; lr = lr1; }
         else if ((x -= n_ch) < n_ea) { pp = p.ea; gg = gr.ea; mm = m.ea; vv = v.ea; lr = lr2; }
         else { x -= n_ea; pp = p.eW; gg = gr.eW; mm = m.eW; vv = v.eW; lr = lr3; }
-        AdamK k{b1, b2, eps, lr / bc1, isb2};
+        AdamK k{be, lr / bc1, isb2};
         float pv = pp[x], mv = mm[x], vv_ = vv[x];
         adam1(pv, gg[x], mv, vv_, k);
         pp[x] = pv; mm[x] = mv; vv[x] = vv_;
@@ -47,13 +51,42 @@ __global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_para
     }
 }
 
+// Per-image Adam coefficients of the current step, formed in FP64 and rounded
+// once: the four step sizes lr_g / (1 - b1^t) (the centre rate follows the
+// exponential schedule) and 1 / sqrt(1 - b2^t).  Threads stride over images.
+__device__ void adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
+                           float *coef) {
+    for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
+        const ImgDev &im = img_of(g, b);
+        const int32_t it = step[b];
+        const double t = (double)(it + 1);
+        const double bc1 = 1.0 - pow(b1, t);
+        const double f = im.iters > 1 ? (double)it / (double)(im.iters - 1) : 0.0;
+        const double lr_mu =
+            im.lr_mu0 > 0.0f ? (double)im.lr_mu0 * pow((double)im.lr_mu1 / im.lr_mu0, f) : 0.0;
+        float *c = coef + 8 * b;
+        c[0] = (float)(lr_mu / bc1);
+        c[1] = (float)(im.lr_chol / bc1);
+        c[2] = (float)(im.lr_ea / bc1);
+        c[3] = (float)(im.lr_eW / bc1);
+        c[4] = (float)(1.0 / sqrt(1.0 - pow(b2, t)));
+    }
+}
+
+__global__ void k_adam_coefs(const __grid_constant__ Geo g, const int32_t *step, double b1,
+                             double b2, float *coef) {
+    adam_coefs(g, step, b1, b2, coef);
+}
+
 // Fit: raw per-kernel sums -> gradients (see render.cu) -> Adam on the 5 + C
 // (+ 2C) parameters of the kernel; zeroes the sums.  The last CTA to finish
-// advances every running image's step counter.
+// advances every running image's step counter and forms the coefficients of
+// the next step.
 __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, float *chol,
                            float *ea, float *eW, float *m_mu, float *m_chol, float *m_ea,
                            float *m_eW, float *v_mu, float *v_chol, float *v_ea, float *v_eW,
-                           float b1, float b2, float eps, int32_t *step, uint32_t *done) {
+                           double b1, double b2, Betas be, int32_t *step, uint32_t *done,
+                           float *coef) {
     if (status_bad(w.status)) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < g.K_total) {
@@ -70,15 +103,12 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, flo
             const float *s = rc.x <= rc.z ? acc : zero;
             const float *r = w.rec + k * g.S;
             const int C = g.C, E = g.linear ? 3 : 1;
-            const float t = (float)(it + 1);
-            const float bc1 = 1.0f - powf(b1, t);
-            const float isb2 = rsqrtf(1.0f - powf(b2, t));
-            const float f = im.iters > 1 ? (float)it / (float)(im.iters - 1) : 0.0f;
-            const float lr_mu = im.lr_mu0 * powf(im.lr_mu1 / im.lr_mu0, f);
-            AdamK kmu{b1, b2, eps, lr_mu / bc1, isb2};
-            AdamK kch{b1, b2, eps, im.lr_chol / bc1, isb2};
-            AdamK kea{b1, b2, eps, im.lr_ea / bc1, isb2};
-            AdamK kew{b1, b2, eps, im.lr_eW / bc1, isb2};
+            const float *cf = coef + 8 * b;
+            const float isb2 = cf[4];
+            AdamK kmu{be, cf[0], isb2};
+            AdamK kch{be, cf[1], isb2};
+            AdamK kea{be, cf[2], isb2};
+            AdamK kew{be, cf[3], isb2};
             float gmx = 0.f, gmy = 0.f;
             if (rc.x <= rc.z) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
             for (int ch = 0; ch < C; ++ch) {
@@ -122,10 +152,12 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, flo
         last = prev == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        for (int b = 0; b < g.B; ++b)
+    if (last) {
+        for (int b = threadIdx.x; b < g.B; b += blockDim.x)
             if (step[b] < img_of(g, b).iters) step[b] += 1;
-        *done = 0u;
+        __syncthreads();
+        adam_coefs(g, step, b1, b2, coef);
+        if (threadIdx.x == 0) *done = 0u;
         __threadfence();
     }
 }
@@ -154,8 +186,8 @@ __global__ void k_sq_error(const float *y, const float *t, int64_t n, int clamp,
 }  // namespace
 
 cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
-                            const smoe_params &v, int C, const float lr[4], float b1, float b2,
-                            float eps, int32_t step, cudaStream_t st) {
+                            const smoe_params &v, int C, const float lr[4], double b1, double b2,
+                            double eps, int32_t step, cudaStream_t st) {
     const int has_w = p.eW != nullptr;
     const int64_t total = p.K * (5 + (int64_t)C * (has_w ? 3 : 1));
     if (total == 0) return cudaSuccess;
@@ -163,21 +195,28 @@ cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const s
     const double isb2 = 1.0 / std::sqrt(1.0 - std::pow((double)b2, (double)step));
     int64_t blocks = (total + 255) / 256;
     if (blocks > 65535) blocks = 65535;
+    const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
     k_adam_soa<<<(unsigned)blocks, 256, 0, st>>>(p.K, C, has_w, p, gr, m, v, lr[0], lr[1],
-                                                 lr[2], lr[3], b1, b2, eps, (float)bc1,
-                                                 (float)isb2);
+                                                 lr[2], lr[3], be, (float)bc1, (float)isb2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
                             float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
-                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, float b1,
-                            float b2, float eps, int32_t *step, uint32_t *done,
+                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, double b1,
+                            double b2, double eps, int32_t *step, uint32_t *done, float *coef,
                             cudaStream_t st) {
     const unsigned blocks = (unsigned)((g.K_total + 255) / 256);
     if (blocks == 0) return cudaSuccess;
+    const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
     k_fit_adam<<<blocks, 256, 0, st>>>(g, w, mu, chol, ea, eW, m_mu, m_chol, m_ea, m_eW, v_mu,
-                                       v_chol, v_ea, v_eW, b1, b2, eps, step, done);
+                                       v_chol, v_ea, v_eW, b1, b2, be, step, done, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
+                              float *coef, cudaStream_t st) {
+    k_adam_coefs<<<1, 256, 0, st>>>(g, step, b1, b2, coef);
     return cudaGetLastError();
 }
 

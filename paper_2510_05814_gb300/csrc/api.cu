@@ -23,8 +23,8 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 
 // Workspace regions, in order; `fit` adds the batch table and the lists.
 struct Layout {
-    size_t rec, rect, tile_cnt, cursor, bsum, pair_tmp, acc;
-    size_t table, tile_off, pair_k, n_pairs, done;
+    size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
+    size_t table, tile_off, pair_k, n_pairs, done, coef;
     size_t total;
 };
 
@@ -38,6 +38,8 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
     L.tile_cnt = take(sizeof(int32_t) * (size_t)tiles);
     L.cursor = take(sizeof(int32_t) * (size_t)tiles);
     L.bsum = take(sizeof(long long) * (size_t)scan_blocks_of(tiles));
+    L.long_q = take(sizeof(int32_t) * (size_t)tiles);
+    L.n_long = take(sizeof(int32_t));
     L.acc = take(sizeof(float) * (size_t)GS * (size_t)K);
     L.pair_tmp = take(sizeof(int32_t) * (size_t)pair_cap);
     if (fit) {
@@ -45,6 +47,7 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
         L.pair_k = take(sizeof(int32_t) * (size_t)pair_cap);
         L.n_pairs = take(sizeof(int64_t));
         L.done = take(sizeof(uint32_t));
+        L.coef = take(sizeof(float) * 8 * (size_t)B);
     }
     L.total = o;
     return L;
@@ -103,6 +106,8 @@ Bufs make_bufs(void *ws, const Layout &L) {
     w.cursor = reinterpret_cast<int32_t *>(b + L.cursor);
     w.bsum = reinterpret_cast<long long *>(b + L.bsum);
     w.pair_tmp = reinterpret_cast<int32_t *>(b + L.pair_tmp);
+    w.long_q = reinterpret_cast<int32_t *>(b + L.long_q);
+    w.n_long = reinterpret_cast<int32_t *>(b + L.n_long);
     w.acc = reinterpret_cast<float *>(b + L.acc);
     return w;
 }
@@ -256,8 +261,8 @@ smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params *p, void 
 }
 
 smoe_status smoe_adam_step(const smoe_params *p, const smoe_params *g, const smoe_params *m,
-                           const smoe_params *v, int32_t C, const float lr[4], float b1, float b2,
-                           float eps, int32_t step, void *stream) {
+                           const smoe_params *v, int32_t C, const float lr[4], double b1,
+                           double b2, double eps, int32_t step, void *stream) {
     if (!p || !g || !m || !v || !lr || step < 1 || (C != 1 && C != 3)) return SMOE_ERR_ARG;
     const smoe_params *all[4] = {p, g, m, v};
     const bool has_w = p->eW != nullptr;
@@ -335,12 +340,17 @@ smoe_status smoe_fit_init(const smoe_fit_batch *batch, const smoe_fit_image *img
             e = cudaMemsetAsync(batch->loss, 0, sizeof(double) * g.B * batch->hist, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     }
+    if (e == cudaSuccess) {
+        if (g.B > 1) g.table = reinterpret_cast<const ImgDev *>(b + L.table);
+        e = launch_adam_coefs(g, batch->step, batch->b1, batch->b2,
+                              reinterpret_cast<float *>(b + L.coef), st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host table is freed on return
     return cuda_status(e);
 }
 
 static cudaError_t fit_phase(const smoe_fit_batch *batch, const Geo &g, const Bufs &w,
-                             uint32_t *done, int phase, cudaStream_t st) {
+                             uint32_t *done, float *coef, int phase, cudaStream_t st) {
     const smoe_params &p = batch->p, &m = batch->m, &v = batch->v;
     switch (phase) {
         case 0: return launch_bin(g, w, st);
@@ -348,7 +358,7 @@ static cudaError_t fit_phase(const smoe_fit_batch *batch, const Geo &g, const Bu
         case 2:
             return launch_fit_adam(g, w, p.mu, p.chol, p.ea, p.eW, m.mu, m.chol, m.ea, m.eW,
                                    v.mu, v.chol, v.ea, v.eW, batch->b1, batch->b2, batch->eps,
-                                   batch->step, done, st);
+                                   batch->step, done, coef, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -364,9 +374,10 @@ smoe_status smoe_fit(const smoe_fit_batch *batch, const smoe_fit_image *imgs, in
     if (s != SMOE_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t *done = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.done);
+    float *coef = reinterpret_cast<float *>(static_cast<char *>(ws) + L.coef);
     for (int32_t it = 0; it < n_iters; ++it)
         for (int phase = 0; phase < 3; ++phase)
-            if (fit_phase(batch, g, w, done, phase, st) != cudaSuccess) return SMOE_ERR_CUDA;
+            if (fit_phase(batch, g, w, done, coef, phase, st) != cudaSuccess) return SMOE_ERR_CUDA;
     return SMOE_OK;
 }
 
@@ -381,7 +392,9 @@ smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_image *im
     smoe_status s = fit_bufs(batch, imgs, pair_cap, ws, ws_bytes, status, &g, &w, &L, &tab);
     if (s != SMOE_OK) return s;
     uint32_t *done = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + L.done);
-    return cuda_status(fit_phase(batch, g, w, done, phase, static_cast<cudaStream_t>(stream)));
+    float *coef = reinterpret_cast<float *>(static_cast<char *>(ws) + L.coef);
+    return cuda_status(
+        fit_phase(batch, g, w, done, coef, phase, static_cast<cudaStream_t>(stream)));
 }
 
 smoe_status smoe_get_status(const int32_t *status, void *stream) {

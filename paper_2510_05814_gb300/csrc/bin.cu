@@ -1,14 +1,16 @@
 // Binning: the "geometry shader" (Sec. IV-B) and the subset kernel selection
 // per block (Sec. IV-C, Eq. 5) as a counting sort of (tile, kernel) pairs.
 //
-//   k_prep_bbox   one thread per kernel: prepared record, tile rectangle,
-//                 per-tile counts (atomic increments)
-//   k_scan_*      exclusive prefix sum of the per-tile counts -> tile_off
-//                 (three phases: block sums, scan of the sums, block scans)
-//   k_scatter     one thread per kernel: claim a slot in each covered tile
-//   k_segsort     one CTA per tile: restore ascending kernel order inside the
-//                 tile (bitonic sort in shared memory, or a bitmap sweep over
-//                 the kernel-id range for very long lists)
+//   k_prep_bbox     one thread per kernel: prepared record, tile rectangle,
+//                   per-tile counts (atomic increments; a large rectangle is
+//                   walked by the whole warp)
+//   k_scan_*        exclusive prefix sum of the per-tile counts -> tile_off
+//                   (three phases: block sums, scan of the sums, block scans)
+//   k_scatter       one thread per kernel: claim a slot in each covered tile
+//   k_segsort_warp  one warp per tile: restore ascending kernel order (register
+//                   bitonic sort for lists of up to 256 ids)
+//   k_segsort_long  one CTA per longer list (bitonic sort in shared memory up
+//                   to 2048 ids, a bitmap sweep over the kernel-id range above)
 //
 // The per-tile lists are the unique sets {k : tile in rect_k} in ascending k,
 // so the output is bit-exact whatever order the atomics took.
@@ -24,11 +26,53 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortMax = 2048;                 // bitonic in shared memory up to this
 constexpr int kBitmapWords = 8192;             // 262144 kernel ids per bitmap pass
+constexpr int kLongGrid = 608;                 // CTAs sweeping the queue of long lists
+
+// Add 1 to the count (or claim a slot) of every tile of the rectangles of
+// the warp's kernels.  Small rectangles are walked by their own lane; a large
+// one (a wide or degenerate kernel, up to the whole image) by the whole warp.
+template <bool SCATTER>
+__device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect, int64_t t_off,
+                                           int tiles_x, int32_t k) {
+    constexpr int kBig = 32;
+    const int lane = threadIdx.x & 31;
+    const int wdt = rect.z - rect.x + 1;
+    const int n = valid && rect.x <= rect.z ? wdt * (rect.w - rect.y + 1) : 0;
+    auto visit = [&](int64_t t, int32_t kid) {
+        if (SCATTER) {
+            const int slot = atomicAdd(&w.cursor[t], 1);
+            w.pair_tmp[(int64_t)w.tile_off[t] + slot] = kid;
+        } else {
+            atomicAdd(&w.tile_cnt[t], 1);
+        }
+    };
+    if (n <= kBig) {
+        for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
+            for (int tx = rect.x; tx <= rect.z; ++tx)
+                visit(t_off + (int64_t)ty * tiles_x + tx, k);
+    }
+    unsigned big = __ballot_sync(0xffffffffu, n > kBig);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const int4 r = make_int4(__shfl_sync(0xffffffffu, rect.x, src),
+                                 __shfl_sync(0xffffffffu, rect.y, src),
+                                 __shfl_sync(0xffffffffu, rect.z, src),
+                                 __shfl_sync(0xffffffffu, rect.w, src));
+        const int64_t to = __shfl_sync(0xffffffffu, t_off, src);
+        const int tx_n = __shfl_sync(0xffffffffu, tiles_x, src);
+        const int32_t kk = __shfl_sync(0xffffffffu, k, src);
+        const int rw = r.z - r.x + 1, nn = rw * (r.w - r.y + 1);
+        for (int i = lane; i < nn; i += 32)
+            visit(to + (int64_t)(r.y + i / rw) * tx_n + r.x + i % rw, kk);
+    }
+}
 
 __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
     if (status_bad(w.status)) return;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= g.K_total) return;
+    const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = k_raw < g.K_total;
+    const int64_t k = valid ? k_raw : g.K_total - 1;   // inactive lanes mirror the last kernel
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
     // Kernel in output-pixel units, one rounding per operation.
     float mx = __fmul_rn(g.mu[2 * k], (float)im.W);
@@ -40,19 +84,21 @@ __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
         b = __fdiv_rn(b, g.scale);
         c = __fdiv_rn(c, g.scale);
     }
-    float *r = w.rec + k * g.S;
-    r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c; r[5] = 0.0f; r[6] = 0.0f;
-    const int E = g.linear ? 3 : 1;
-    for (int ch = 0; ch < g.C; ++ch) {
-        r[7 + ch * E] = g.ea[k * g.C + ch];
-        if (g.linear) {
-            float w0 = g.eW[(k * g.C + ch) * 2], w1 = g.eW[(k * g.C + ch) * 2 + 1];
-            if (scaled) { w0 = __fdiv_rn(w0, g.scale); w1 = __fdiv_rn(w1, g.scale); }
-            r[7 + ch * E + 1] = w0;
-            r[7 + ch * E + 2] = w1;
+    if (valid) {
+        float *r = w.rec + k * g.S;
+        r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c; r[5] = 0.0f; r[6] = 0.0f;
+        const int E = g.linear ? 3 : 1;
+        for (int ch = 0; ch < g.C; ++ch) {
+            r[7 + ch * E] = g.ea[k * g.C + ch];
+            if (g.linear) {
+                float w0 = g.eW[(k * g.C + ch) * 2], w1 = g.eW[(k * g.C + ch) * 2 + 1];
+                if (scaled) { w0 = __fdiv_rn(w0, g.scale); w1 = __fdiv_rn(w1, g.scale); }
+                r[7 + ch * E + 1] = w0;
+                r[7 + ch * E + 2] = w1;
+            }
         }
+        for (int x = 7 + g.C * E; x < g.S; ++x) r[x] = 0.0f;
     }
-    for (int x = 7 + g.C * E; x < g.S; ++x) r[x] = 0.0f;
 
     // Bounding box: square of half side r = sqrt(q_max * lambda_max(Sigma))
     // * (1 + 2^-10), lambda_max(Sigma) = lambda_max(P) / det(P), P = L L^T.
@@ -98,10 +144,8 @@ __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
                 rect = make_int4((int)fx0, (int)fy0, (int)fx1, (int)fy1);
         }
     }
-    w.rect[k] = rect;
-    for (int ty = rect.y; ty <= rect.w; ++ty)
-        for (int tx = rect.x; tx <= rect.z; ++tx)
-            atomicAdd(&w.tile_cnt[im.t_off + (int64_t)ty * im.tiles_x + tx], 1);
+    if (valid) w.rect[k] = rect;
+    walk_rects<false>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k);
 }
 
 // Block-wide exclusive scan of one long long per thread (1024 threads).
@@ -149,7 +193,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(int64_t n, const i
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(int nb, long long *bsum, int64_t n,
                                                            int32_t *tile_off, int64_t *n_pairs,
-                                                           int64_t cap, int32_t *status) {
+                                                           int32_t *n_long, int64_t cap,
+                                                           int32_t *status) {
     if (status_bad(status)) return;
     // nb <= kScanChunk: each thread scans up to kScanItems consecutive sums.
     const int base = threadIdx.x * kScanItems;
@@ -168,6 +213,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(int nb, long long *bs
     }
     if (threadIdx.x == 0) {
         *n_pairs = total;
+        *n_long = 0;
         tile_off[n] = (int32_t)(total < cap ? total : cap);
         if (total > cap) atomicCAS(status, 0, (int32_t)SMOE_ERR_CAPACITY);
     }
@@ -200,17 +246,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const int
 
 __global__ void k_scatter(const __grid_constant__ Geo g, Bufs w) {
     if (status_bad(w.status)) return;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= g.K_total) return;
+    const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool valid = k_raw < g.K_total;
+    const int64_t k = valid ? k_raw : g.K_total - 1;
     const int4 rect = w.rect[k];
-    if (rect.x > rect.z) return;
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
-    for (int ty = rect.y; ty <= rect.w; ++ty)
-        for (int tx = rect.x; tx <= rect.z; ++tx) {
-            const int64_t t = im.t_off + (int64_t)ty * im.tiles_x + tx;
-            const int slot = atomicAdd(&w.cursor[t], 1);
-            w.pair_tmp[(int64_t)w.tile_off[t] + slot] = (int32_t)k;
-        }
+    walk_rects<true>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k);
 }
 
 __device__ int block_exscan_int(int v, int *total) {
@@ -234,10 +275,79 @@ __device__ int block_exscan_int(int v, int *total) {
     return base + x - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_segsort(const __grid_constant__ Geo g, Bufs w) {
+__device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s);
+
+// One warp per tile: lists of up to 256 ids are sorted in registers (8 per
+// lane, bitonic network, lane-crossing stages by shuffles); longer lists are
+// queued for k_segsort_long.
+__global__ void __launch_bounds__(256) k_segsort_warp(int64_t n_tiles, Bufs w) {
+    if (status_bad(w.status)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= n_tiles) return;
+    const int64_t start = w.tile_off[t];
+    const int n = (int)(w.tile_off[t + 1] - start);
+    if (n <= 1) {
+        if (n == 1 && lane == 0) w.pair_k[start] = w.pair_tmp[start];
+        return;
+    }
+    if (n > 256) {
+        if (lane == 0) w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
+        return;
+    }
+    int v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = lane * 8 + i;
+        v[i] = p < n ? w.pair_tmp[start + p] : 0x7fffffff;
+    }
+#pragma unroll
+    for (int k = 2; k <= 256; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 8) {
+                const int lj = j >> 3;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool up = ((lane * 8 + i) & k) == 0;
+                    const int o = __shfl_xor_sync(0xffffffffu, v[i], lj);
+                    v[i] = (lower == up) ? min(v[i], o) : max(v[i], o);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int ip = i ^ j;
+                    if (ip > i) {
+                        const bool up = ((lane * 8 + i) & k) == 0;
+                        const int a = v[i], b = v[ip];
+                        v[i] = up ? min(a, b) : max(a, b);
+                        v[ip] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int p = lane * 8 + i;
+        if (p < n) w.pair_k[start + p] = v[i];
+    }
+}
+
+// One CTA per queued long list (grid-stride over the queue).
+__global__ void __launch_bounds__(kSortThreads) k_segsort_long(const __grid_constant__ Geo g,
+                                                               Bufs w) {
     if (status_bad(w.status)) return;
     __shared__ uint32_t s[kBitmapWords];
-    const int64_t t = blockIdx.x;
+    const int n_long = *w.n_long;
+    for (int q = blockIdx.x; q < n_long; q += gridDim.x) {
+        segsort_tile(g, w, w.long_q[q], s);
+        __syncthreads();
+    }
+}
+
+__device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s) {
     const int64_t start = w.tile_off[t];
     const int n = (int)(w.tile_off[t + 1] - start);
     if (n <= 0) return;
@@ -307,15 +417,19 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     }
     const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.status);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(nb, w.bsum, n, w.tile_off, w.n_pairs, w.pair_cap,
-                                           w.status);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(nb, w.bsum, n, w.tile_off, w.n_pairs, w.n_long,
+                                           w.pair_cap, w.status);
     k_scan_down<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.tile_off, w.cursor,
                                              w.pair_cap, w.status);
     if (g.K_total > 0) {
         const unsigned gb = (unsigned)((g.K_total + 255) / 256);
         k_scatter<<<gb, 256, 0, st>>>(g, w);
     }
-    k_segsort<<<(unsigned)n, kSortThreads, 0, st>>>(g, w);
+    if (n > 0) {
+        k_segsort_warp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, w);
+        const int64_t gl = n < kLongGrid ? n : kLongGrid;
+        k_segsort_long<<<(unsigned)gl, kSortThreads, 0, st>>>(g, w);
+    }
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct Bufs {
     int32_t *cursor;
     long long *bsum;
     int32_t *pair_tmp;
+    int32_t *long_q;     // tiles whose list is too long for the warp sort
+    int32_t *n_long;
     float *acc;
     int32_t *tile_off;
     int32_t *pair_k;
@@ -129,13 +131,15 @@ cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const
 cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,
                              const int32_t *step, cudaStream_t st);
 cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
-                            const smoe_params &v, int C, const float lr[4], float b1, float b2,
-                            float eps, int32_t step, cudaStream_t st);
+                            const smoe_params &v, int C, const float lr[4], double b1, double b2,
+                            double eps, int32_t step, cudaStream_t st);
 cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
                             float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
-                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, float b1,
-                            float b2, float eps, int32_t *step, uint32_t *done,
+                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, double b1,
+                            double b2, double eps, int32_t *step, uint32_t *done, float *coef,
                             cudaStream_t st);
+cudaError_t launch_adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
+                              float *coef, cudaStream_t st);
 cudaError_t launch_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out,
                             cudaStream_t st);
 

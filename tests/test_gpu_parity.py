@@ -5,7 +5,7 @@ Bar (element by element on the same seeded inputs):
   - render: |y - y_ref| <= 1e-5 * max(|y_ref|, sum_k w_k |m_k|) per pixel and
     channel (FP32 against the FP64 oracle), 1/D within 1e-5 relative;
   - gradients: per element |g - g_ref| <= 1e-4 * max(|g_ref|, 1e-3 * max|g_ref|
-    of the group);
+    of the group, 1e-2 * the sum of the magnitudes of the element's terms);
   - Adam: within FP32 rounding of the FP64 update.
 """
 import numpy as np
@@ -103,12 +103,19 @@ def check_y(y, ref, scale, what=""):
     assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} over tolerance, max err {err.max()}"
 
 
-def check_grad(g, ref, what=""):
+def check_grad(g, ref, what="", terms=None, rtol=RTOL_G):
+    """Relative error with the denominator floored at 1e-3 x the group's
+    largest gradient and, where `terms` (the oracle's sum of term
+    magnitudes) is given, at 1e-2 x that sum: an element whose exact value
+    cancels to ~0 (e.g. the gate terms of a single kernel, where y == m) is
+    held to FP32 noise relative to the terms that cancel."""
     ref = np.asarray(ref, np.float64)
     floor = 1e-3 * np.abs(ref).max() if ref.size else 0.0
     den = np.maximum(np.abs(ref), floor)
+    if terms is not None:
+        den = np.maximum(den, 1e-2 * np.asarray(terms, np.float64))
     rel = np.abs(np.asarray(g, np.float64) - ref) / np.where(den > 0, den, 1.0)
-    assert rel.max() <= RTOL_G, f"{what}: max rel err {rel.max():.3g}"
+    assert rel.max() <= rtol, f"{what}: max rel err {rel.max():.3g}"
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"c{c[0]}" for c in CASES])
@@ -142,10 +149,11 @@ def test_backward_parity(case):
     gy = rng.normal(0, 1, (C, H, W))
     g = r.backward(params, y, invd, gy=torch.tensor(gy, dtype=torch.float32, device="cuda"))
     gy32 = gy.astype(np.float32).astype(np.float64)
-    ref = om.backward(oracle_model(p, W, H, C, tile, scale=scale), gy=gy32)
-    for name, a, b in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref):
+    ref, terms = om.backward(oracle_model(p, W, H, C, tile, scale=scale), gy=gy32,
+                             with_scale=True)
+    for name, a, b, t in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref, terms):
         if b is not None:
-            check_grad(a, b, name)
+            check_grad(a, b, name, t)
 
 
 def test_fused_mse_backward_parity():
@@ -154,9 +162,9 @@ def test_fused_mse_backward_parity():
     y, invd = r.render()
     t = synth.polygon_image(72, 60, 3, 5, 21)
     g = r.backward(params, y, invd, target=torch.tensor(t, device="cuda"))
-    ref = om.backward(oracle_model(p, 72, 60, 3, 16), target=t)
-    for name, a, b in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref):
-        check_grad(a, b, name)
+    ref, terms = om.backward(oracle_model(p, 72, 60, 3, 16), target=t, with_scale=True)
+    for name, a, b, s_ in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref, terms):
+        check_grad(a, b, name, s_)
 
 
 def test_long_lists_use_bitmap_path():
@@ -172,6 +180,14 @@ def test_long_lists_use_bitmap_path():
     y, invd = r.render()
     ref, _, absm = om.render(m, with_scale=True)
     check_y(y.cpu().numpy(), ref, absm, "y")
+    gy = np.random.default_rng(32).normal(0, 1, (1, 40, 40))
+    g = r.backward(params, y, invd, gy=torch.tensor(gy, dtype=torch.float32, device="cuda"))
+    ref_g, terms = om.backward(m, gy=gy.astype(np.float32).astype(np.float64), with_scale=True)
+    # ~3000 kernels are in range at every pixel here: the FP32 sums D and
+    # N_c carry a relative error of order n * 2^-24 ~ 2e-4, so this stress
+    # case is held to 1e-3 instead of 1e-4.
+    for name, a, b, t in zip(["mu", "chol", "ea"], g.numpy(), ref_g, terms):
+        check_grad(a, b, name, t, rtol=1e-3)
 
 
 def test_empty_model_and_offimage_kernels():
@@ -224,6 +240,7 @@ def test_adam_parity():
     lr = (1e-2, 1e-3, 2e-3, 5e-4)
     ref = [[t.cpu().numpy().astype(np.float64).ravel().copy() for t in x.tensors()] for x in (p, m, v)]
     for step in (1, 2, 3):
+        prev = [x.copy() for x in ref[0]]
         g = mk()
         gref = [t.cpu().numpy().astype(np.float64).ravel() for t in g.tensors()]
         api.smoe_adam_step(p, g, m, v, lr, 0.9, 0.999, 1e-8, step)
@@ -232,7 +249,10 @@ def test_adam_parity():
         assert all(torch.count_nonzero(t).item() == 0 for t in g.tensors())   # grads zeroed
         for gi, t in enumerate(p.tensors()):
             got = t.cpu().numpy().astype(np.float64).ravel()
-            assert np.all(np.abs(got - ref[0][gi]) <= 4e-7 * np.abs(ref[0][gi]) + 1e-5 * lr[gi])
+            # FP32 rounding of the result and of the update (which is large
+            # where v is tiny)
+            upd = np.abs(ref[0][gi] - prev[gi])
+            assert np.all(np.abs(got - ref[0][gi]) <= 4e-7 * (np.abs(ref[0][gi]) + upd) + 1e-12)
             # continue from the GPU state so rounding does not accumulate
             ref[0][gi] = got.copy()
             ref[1][gi] = m.tensors()[gi].cpu().numpy().astype(np.float64).ravel().copy()

@@ -404,6 +404,19 @@ def test_backward_fused_mse_and_selected_kernels(om):
         np.testing.assert_allclose(w, x[sel], rtol=1e-12, atol=1e-18)
 
 
+def test_backward_term_scale_bounds_gradient(om):
+    """The optional term-magnitude sums bound the gradients (triangle
+    inequality) and equal them for a single all-positive term."""
+    rng = np.random.default_rng(12)
+    m = rand_model(om, rng, W=20, H=18, K=8)
+    gy = rng.normal(0, 1, (m.C, m.H, m.W))
+    g, s = om.backward(m, gy=gy, with_scale=True)
+    for a, b in zip(g, s):
+        assert np.all(np.abs(a) <= b * (1 + 1e-12) + 1e-300)
+    g2, s2 = om.backward(m, gy=np.abs(gy), with_scale=True)
+    np.testing.assert_allclose(np.abs(g2[2]), s2[2], rtol=1e-12)   # ea: terms g*|G| >= 0
+
+
 def test_backward_central_differences(om):
     """Central differences of the oracle's own FP64 render agree with its
     analytic gradient on parameters whose inclusion pattern does not change."""
