@@ -219,6 +219,28 @@ SMOE_API smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_
                                     int64_t pair_cap, void *ws, size_t ws_bytes, int32_t phase,
                                     int32_t *status, void *stream);
 
+/* Bin and render one model without allocating anything: for callers that
+ * cannot call cudaMalloc (a plugin inside an application that owns every
+ * device allocation, code that must not touch the allocator).  The paper has
+ * no counterpart; it is smoe_bin followed by smoe_render with every
+ * intermediate buffer in one fixed 8 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   Limits: K <= 32768 kernels, at most 16384 tiles on the output raster
+ *   (e.g. 2048x2048 at tile 16), at most 524288 (tile, kernel) pairs.
+ *   Larger K or rasters are refused with SMOE_ERR_WORKSPACE before any work;
+ *   a pair count above the limit sets *status = SMOE_ERR_CAPACITY on the
+ *   device and y / inv_d are then not written.
+ *   p      parameters (device SoA); y: C x H x W out; inv_d: H x W out or NULL
+ *   status out: one int32 (device), zeroed by the call, then as smoe_bin.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads on one device) race: serialise them.
+ * The call itself allocates nothing and does not synchronise. */
+SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smoe_params *p, float *y,
+                                        float *inv_d, int32_t *status, void *stream);
+
 /* Synchronise `stream` and return the device status word (SMOE_OK, or the
  * first data-dependent error), or SMOE_ERR_CUDA if the stream failed. */
 SMOE_API smoe_status smoe_get_status(const int32_t *status, void *stream);

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsmoe.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["bin.cu", "render.cu", "adam.cu", "api.cu"]
+SOURCES = ["bin.cu", "render.cu", "adam.cu", "api.cu", "static_render.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
