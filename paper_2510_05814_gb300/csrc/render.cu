@@ -1,27 +1,38 @@
-// Tile kernels of the rasterised SMoE regression.
+// Tile kernels of the rasterised SMoE regression: forward render (Eqs. 2-5),
+// the backward of the gradient-descent fit through the rasteriser
+// (Sec. III-D), and the fused forward + MSE + backward fit tile.
 //
-// Forward (Eqs. 2-5, per tile, pixel-major): each lane owns a few pixels of
-// the tile and walks the tile's kernel list, keeping the gate denominator
-// D = sum e and the numerators N_c = sum e m_c in FP32 registers; the warps of
-// a CTA split the list (T = 8, 16) or the tile (T = 32) and meet in shared
-// memory at the end.  Kernel records are staged per warp in shared memory,
-// 32 at a time, and the next 32 are fetched into registers while the current
-// ones are evaluated.
+// One CTA (4 warps) per tile.  The tile's kernel list is processed in chunks
+// of up to NCH kernels; each chunk is staged in shared memory: the kernel's
+// prepared record and a ROW MASK, bit r set iff row r of the tile can hold an
+// included pixel.  The row test is exact: with the predicate's own FP32
+// values, q32 = fma(z0, z0, u) >= u = (c dy)^2 for every pixel of the row, so
+// a row with u > q_max holds no included pixel and skipping it changes no
+// result.
 //
-// Backward (the gradient-descent fit through the rasteriser, Sec. III-D;
-// kernel-major): each lane owns ONE kernel of the tile's list and walks the
-// tile's pixels, whose per-pixel upstream state sits in shared memory, so the
-// per-kernel sums need no cross-lane reduction.  Gates are recomputed.  The
-// sums are raw moments (below); a finalize pass turns them into gradients.
-// One float4 atomic add per 4 sums per (tile, kernel).
+// Forward (pixel-major): a warp owns a band of 64 pixels (2 adjacent pixels
+// per lane, 64/T rows) and walks the chunk, skipping every kernel whose mask
+// misses the band's rows; D = sum e and N_c = sum e m_c stay in FP32
+// registers.  Pixel pairs use packed f32x2 arithmetic (IEEE per lane, the
+// same single rounding as the scalar predicate, so the inclusion decision is
+// bit-identical).  T = 8 has one band: its warps split the chunk and meet in
+// shared memory.
 //
-// Raw per-kernel sums (s = g * sum_c G_c (m_c - y_c), g = e / D,
-// H_c = G_c / D, so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c):
+// Backward (item-major): every (row, kernel) pair of the chunk with its mask
+// bit set is one item; the CTA's threads take items in row-major order (so a
+// warp's lanes read the same row of pixel state, a broadcast, and add into
+// different kernels' sums).  An item walks the row's T pixels (packed pairs),
+// recomputes the gate and accumulates the raw moments below, adds them to the
+// kernel's sums in shared memory, and after the chunk one float4 atomic per 4
+// sums per (tile, kernel) goes to the global accumulator.
+//
+// Raw per-kernel sums (s = g sum_c G_c (m_c - y_c), g = e / D, H_c = G_c / D,
+// so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c):
 //   [0] A1 = sum s z0 dx  [1] B1 = sum s z0 dy  [2] C1 = sum s z1 dy
 //   [3] A2 = sum s z0     [4] Z3 = sum s z1
 //   [5+c] E_c = sum e H_c,   linear: [5+C+c] F_c = sum e H_c dx,
 //                                    [5+2C+c] Fy_c = sum e H_c dy
-// and the gradients (Sec. III-D chain rule of Eqs. 2-4):
+// and the gradients (chain rule of Eqs. 2-4):
 //   dL/da = -A1, dL/db = -B1, dL/dc = -C1,
 //   dL/dmx = a A2 - sum_c W_c0 E_c,  dL/dmy = b A2 + c Z3 - sum_c W_c1 E_c,
 //   dL/dea_c = E_c, dL/dW_c0 = F_c, dL/dW_c1 = Fy_c.
@@ -33,25 +44,55 @@ namespace {
 
 constexpr int kNW = 4;                // warps per CTA
 constexpr int kThreads = kNW * 32;
-
-template <int T>
-struct Shape {
-    static constexpr int SUB = T >= 16 ? 16 : 8;       // side of one warp's pixel block
-    static constexpr int NSUB = (T / SUB) * (T / SUB);  // pixel blocks per tile
-    static constexpr int KSPLIT = kNW / NSUB;           // warps sharing a pixel block
-    static constexpr int PX = SUB / 4;                  // pixels per lane along a row
-    static constexpr int RY = SUB / 8;                  // rows per lane
-    static constexpr int NPX = PX * RY;
-};
+// Resident CTAs per SM that the register budget targets, and the chunk of a
+// tile's list staged in shared memory at once (tiles of 8 and 16 pixels).
+#ifndef SMOE_MIN_BLOCKS
+#define SMOE_MIN_BLOCKS 4
+#endif
+#ifndef SMOE_NCH
+#define SMOE_NCH 256
+#endif
+constexpr int kMinBlocks = SMOE_MIN_BLOCKS;
 
 template <int C, bool LIN>
 struct Rec {
     static constexpr int E = LIN ? 3 : 1;
-    static constexpr int S = (7 + C * E + 3) & ~3;
-    static constexpr int GS = (5 + C * E + 3) & ~3;
+    static constexpr int S = (7 + C * E + 3) & ~3;        // global record stride (floats)
+    static constexpr int SS = (S % 8 == 0) ? S + 4 : S;   // shared stride: spreads banks
+    static constexpr int GS = (5 + C * E + 3) & ~3;       // accumulator stride (raw sums)
 };
 
-// Tile coordinates of global tile t.
+template <int C, int T>
+struct Geom {
+    static constexpr int NPX = T * T;
+    static constexpr int BANDS = NPX / 64;                // 64-pixel bands per tile
+    static constexpr int BROWS = 64 / T;                  // rows per band
+    static constexpr int LROW = T / 2;                    // lanes per row (2 px each)
+    static constexpr int KSPLIT = BANDS >= kNW ? 1 : kNW / BANDS;
+    static constexpr int BPW = BANDS >= kNW ? BANDS / kNW : 1;   // bands per warp
+    static constexpr int NCH = T >= 32 ? 128 : SMOE_NCH;  // kernels per chunk
+    static constexpr int PS = 2 * (C + 1);                // floats per pixel pair of state
+    static constexpr int RS = (T / 2) * PS + 4;           // floats per row of state (padded)
+};
+
+template <int C, bool LIN, int T>
+struct Smem {
+    using R = Rec<C, LIN>;
+    using G = Geom<C, T>;
+    alignas(16) float rec[G::NCH * R::SS];
+    alignas(16) float pst[T * G::RS];
+    alignas(16) float red[(G::KSPLIT - 1) * (C + 1) * G::NPX + 1];
+    uint32_t mask[G::NCH];
+    int32_t kid[G::NCH];
+    uint8_t flist[kNW][G::NCH];          // per-warp compacted kernel list of a band
+    uint8_t order[G::NCH];               // backward: kernels grouped by first row
+    int bcnt[T + 1], boff[T + 1];
+    double lsum[kNW];
+};
+
+template <int C, bool LIN, int T>
+constexpr size_t smem_bytes() { return sizeof(Smem<C, LIN, T>); }
+
 struct TileInfo {
     int b, x0, y0, W, H;
     int64_t start;
@@ -72,390 +113,519 @@ __device__ __forceinline__ TileInfo tile_info(const Geo &g, const Bufs &w, int64
     return ti;
 }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Stage kernels [c0, c0 + nc) of the tile's list: records and row masks.
+template <int C, bool LIN, int T>
+__device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const TileInfo &ti,
+                                            int c0, int nc, Smem<C, LIN, T> &sm) {
+    using R = Rec<C, LIN>;
+    constexpr int Q = R::S / 4;                // float4 per record
+    for (int i = threadIdx.x; i < nc * Q; i += kThreads) {
+        const int j = i / Q, q = i - j * Q;
+        const int kid = w.pair_k[ti.start + c0 + j];
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(w.rec + (int64_t)kid * R::S) + q);
+        *reinterpret_cast<float4 *>(sm.rec + j * R::SS + 4 * q) = v;
+        if (q == 0) sm.kid[j] = kid;
+    }
+    __syncthreads();
+    // Row masks: u = (c dy)^2 with the predicate's FP32 operations.
+    for (int j = threadIdx.x; j < nc; j += kThreads) {
+        const float my = sm.rec[j * R::SS + 1], c = sm.rec[j * R::SS + 4];
+        const float y0f = (float)ti.y0 + 0.5f;
+        uint32_t m = 0;
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+            const float dy = __fsub_rn(__fadd_rn(y0f, (float)r), my);
+            const float z1 = __fmul_rn(c, dy);
+            const float u = __fmul_rn(z1, z1);
+            m |= (u <= g.qmax ? 1u : 0u) << r;
+        }
+        sm.mask[j] = m;
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- forward
 
-template <int C, bool LIN, int T>
-__device__ __forceinline__ void fwd_accumulate(const Geo &g, const float *__restrict__ rec,
-                                               const int32_t *__restrict__ list, int n,
-                                               float x0_px, float y0_px, float *stage,
-                                               float (&D)[Shape<T>::NPX],
-                                               float (&N)[C][Shape<T>::NPX]) {
-    using Sh = Shape<T>;
+// One kernel's contribution to a lane's two pixels (row y0, columns x2).
+template <int C, bool LIN>
+__device__ __forceinline__ void fwd_pair(const float *r, float y0, float2 x2, float qmax,
+                                         float2 &D, float2 (&N)[C]) {
     using R = Rec<C, LIN>;
-    constexpr int S = R::S;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int split = warp % Sh::KSPLIT;
-    const int lr = lane >> 2, lc = lane & 3;
-    float xc[Sh::PX], yc[Sh::RY];
+    const float4 r0 = *reinterpret_cast<const float4 *>(r);
+    const float4 r1 = *reinterpret_cast<const float4 *>(r + 4);
+    float ex[R::SS - 8 > 0 ? R::SS - 8 : 1];
+    if (R::S > 8) {
 #pragma unroll
-    for (int px = 0; px < Sh::PX; ++px) xc[px] = x0_px + (float)(lc * Sh::PX + px) + 0.5f;
-#pragma unroll
-    for (int ry = 0; ry < Sh::RY; ++ry) yc[ry] = y0_px + (float)(lr + 8 * ry) + 0.5f;
-#pragma unroll
-    for (int i = 0; i < Sh::NPX; ++i) {
-        D[i] = 0.0f;
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) N[ch][i] = 0.0f;
+        for (int q = 0; q < (R::S - 8) / 4; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(r + 8 + 4 * q);
+            ex[4 * q] = v.x; ex[4 * q + 1] = v.y; ex[4 * q + 2] = v.z; ex[4 * q + 3] = v.w;
+        }
     }
+    // record: [0..4] mx my a b c, [5..6] spare, [7 + ch*E + k] experts
+    auto rv = [&](int i) -> float {
+        return i < 4 ? (i == 0 ? r0.x : i == 1 ? r0.y : i == 2 ? r0.z : r0.w)
+             : i < 8 ? (i == 4 ? r1.x : i == 5 ? r1.y : i == 6 ? r1.z : r1.w)
+                     : ex[i - 8];
+    };
+    const float mx = r0.x, my = r0.y, a = r0.z, b = r0.w, c = r1.x;
+    const float dy = __fsub_rn(y0, my);
+    const float t = __fmul_rn(b, dy);
+    const float z1 = __fmul_rn(c, dy);
+    const float u = __fmul_rn(z1, z1);
+    const float2 dx = __fadd2_rn(x2, f2(-mx));
+    const float2 z0 = __ffma2_rn(f2(a), dx, f2(t));
+    const float2 q = __ffma2_rn(z0, z0, f2(u));
+    const float2 arg = __fmul2_rn(q, f2(kNegHalfLog2e));
+    float2 e = make_float2(ex2(arg.x), ex2(arg.y));
+    e.x = q.x <= qmax ? e.x : 0.0f;
+    e.y = q.y <= qmax ? e.y : 0.0f;
+    D = __fadd2_rn(D, e);
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+        const float ea = rv(7 + ch * R::E);
+        float2 m;
+        if (LIN) {
+            const float mb = fmaf(rv(7 + ch * R::E + 2), dy, ea);
+            m = __ffma2_rn(f2(rv(7 + ch * R::E + 1)), dx, f2(mb));
+        } else {
+            m = f2(ea);
+        }
+        N[ch] = __ffma2_rn(e, m, N[ch]);
+    }
+}
+
+// Accumulate D and N_c of one lane's two pixels (row `row`, columns col,
+// col+1 of the tile) over the staged kernels j = j0, j0 + step, ... whose
+// mask meets `band_mask`: the warp first compacts those kernels (ballot),
+// then evaluates them two at a time with independent accumulators.
+template <int C, bool LIN, int T>
+__device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
+                                         Smem<C, LIN, T> &sm, int nc, int j0, int step,
+                                         uint32_t band_mask, int row, int col, float2 &D,
+                                         float2 (&N)[C]) {
+    using R = Rec<C, LIN>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint8_t *lst = sm.flist[warp];
+    int cnt = 0;
+    for (int base = 0; base < nc; base += 32) {
+        const int j = base + lane;
+        const bool hit = j < nc && (j - j0) % step == 0 && j >= j0 && (sm.mask[j] & band_mask);
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
+        cnt += __popc(bal);
+    }
+    __syncwarp();
     const float qmax = g.qmax;
-    const int nchunk = (n + 31) >> 5;
-    float4 nxt[S / 4];
+    const float y0 = (float)(ti.y0 + row) + 0.5f;
+    const float2 x2 = make_float2((float)(ti.x0 + col) + 0.5f, (float)(ti.x0 + col) + 1.5f);
+    float2 D2 = f2(0.0f), N2[C];
 #pragma unroll
-    for (int q = 0; q < S / 4; ++q) nxt[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int ci = split;
-    if (ci < nchunk) {
-        const int j = ci * 32 + lane;
-        if (j < n) {
-            const float4 *src = reinterpret_cast<const float4 *>(rec + (int64_t)list[j] * S);
+    for (int ch = 0; ch < C; ++ch) N2[ch] = f2(0.0f);
+    int i = 0;
+    for (; i + 1 < cnt; i += 2) {
+        fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(sm.rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
+    }
+    if (i < cnt) fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+    D = __fadd2_rn(D, D2);
 #pragma unroll
-            for (int q = 0; q < S / 4; ++q) nxt[q] = __ldg(src + q);
+    for (int ch = 0; ch < C; ++ch) N[ch] = __fadd2_rn(N[ch], N2[ch]);
+    __syncwarp();
+}
+
+// Forward over the whole list.  On return, for every band b the warp owns
+// (bands w, w + 4, ...; T = 8: band 0 summed over the warps), lane l holds
+// D and N_c of pixels (row, col), (row, col + 1) in Dv[bi], Nv[bi].
+template <int C, bool LIN, int T>
+__device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
+                                         Smem<C, LIN, T> &sm, float2 (&Dv)[Geom<C, T>::BPW],
+                                         float2 (&Nv)[Geom<C, T>::BPW][C]) {
+    using G = Geom<C, T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int split = warp % G::KSPLIT;
+#pragma unroll
+    for (int bi = 0; bi < G::BPW; ++bi) {
+        Dv[bi] = f2(0.0f);
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) Nv[bi][ch] = f2(0.0f);
+    }
+    for (int c0 = 0; c0 < ti.n; c0 += G::NCH) {
+        const int nc = min(G::NCH, ti.n - c0);
+        if (c0 > 0) __syncthreads();              // previous chunk fully consumed
+        stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
+#pragma unroll
+        for (int bi = 0; bi < G::BPW; ++bi) {
+            const int band = G::KSPLIT > 1 ? 0 : warp + bi * kNW;
+            const int row = band * G::BROWS + lane / G::LROW;
+            const int col = 2 * (lane % G::LROW);
+            const uint32_t bm = (G::BROWS >= 32 ? 0xffffffffu : ((1u << G::BROWS) - 1u))
+                                << (band * G::BROWS);
+            fwd_band<C, LIN, T>(g, ti, sm, nc, split, G::KSPLIT, bm, row, col, Dv[bi], Nv[bi]);
         }
     }
-    for (; ci < nchunk; ci += Sh::KSPLIT) {
-        __syncwarp();
-        float4 *dst = reinterpret_cast<float4 *>(stage + lane * S);
-#pragma unroll
-        for (int q = 0; q < S / 4; ++q) dst[q] = nxt[q];
-        __syncwarp();
-        const int cnt = min(32, n - ci * 32);
-        const int cn = ci + Sh::KSPLIT;
-        if (cn < nchunk) {
-            const int j = cn * 32 + lane;
-            if (j < n) {
-                const float4 *src = reinterpret_cast<const float4 *>(rec + (int64_t)list[j] * S);
-#pragma unroll
-                for (int q = 0; q < S / 4; ++q) nxt[q] = __ldg(src + q);
-            }
-        }
-        for (int kk = 0; kk < cnt; ++kk) {
-            const float *r = stage + kk * S;
-            const float4 r0 = *reinterpret_cast<const float4 *>(r);
-            const float mx = r0.x, my = r0.y, a = r0.z, b = r0.w;
-            const float c = r[4];
-            float ea[C], w0[C], w1[C];
+    if (G::KSPLIT > 1) {
+        // T = 8: warps 1..3 hand their partial sums to warp 0.
+        const int p = 2 * lane;                   // pixel index of the lane's pair (band 0)
+        if (split > 0) {
+            float *dst = sm.red + (split - 1) * (C + 1) * G::NPX;
+            dst[p] = Dv[0].x;
+            dst[p + 1] = Dv[0].y;
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                ea[ch] = r[7 + ch * R::E];
-                w0[ch] = LIN ? r[7 + ch * R::E + 1] : 0.0f;
-                w1[ch] = LIN ? r[7 + ch * R::E + 2] : 0.0f;
+                dst[(1 + ch) * G::NPX + p] = Nv[0][ch].x;
+                dst[(1 + ch) * G::NPX + p + 1] = Nv[0][ch].y;
             }
-            float dx[Sh::PX];
+        }
+        __syncthreads();
+        if (split == 0) {
 #pragma unroll
-            for (int px = 0; px < Sh::PX; ++px) dx[px] = __fsub_rn(xc[px], mx);
+            for (int k = 0; k < G::KSPLIT - 1; ++k) {
+                const float *src = sm.red + k * (C + 1) * G::NPX;
+                Dv[0].x += src[p];
+                Dv[0].y += src[p + 1];
 #pragma unroll
-            for (int ry = 0; ry < Sh::RY; ++ry) {
-                const float dy = __fsub_rn(yc[ry], my);
-                const float t = __fmul_rn(b, dy);
-                const float z1 = __fmul_rn(c, dy);
-                const float u = __fmul_rn(z1, z1);
-                float mb[C];
-#pragma unroll
-                for (int ch = 0; ch < C; ++ch) mb[ch] = LIN ? fmaf(w1[ch], dy, ea[ch]) : ea[ch];
-#pragma unroll
-                for (int px = 0; px < Sh::PX; ++px) {
-                    float z0;
-                    const float q = q_of(a, dx[px], t, u, z0);
-                    const float e = gate_e(q, qmax);
-                    const int i = ry * Sh::PX + px;
-                    D[i] += e;
-#pragma unroll
-                    for (int ch = 0; ch < C; ++ch) {
-                        const float m = LIN ? fmaf(w0[ch], dx[px], mb[ch]) : mb[ch];
-                        N[ch][i] = fmaf(e, m, N[ch][i]);
-                    }
+                for (int ch = 0; ch < C; ++ch) {
+                    Nv[0][ch].x += src[(1 + ch) * G::NPX + p];
+                    Nv[0][ch].y += src[(1 + ch) * G::NPX + p + 1];
                 }
             }
         }
     }
 }
 
-// Shared memory for the forward phase.
-template <int C, bool LIN, int T>
-struct FwdSmem {
-    float stage[kNW][32 * Rec<C, LIN>::S];
-    float red[Shape<T>::KSPLIT][C + 1][T * T];
-};
-
-// Run the forward over one tile and leave per-pixel D and N_c (summed over
-// the warps sharing a pixel) in red[0][.][px] for px in [0, T*T).
-template <int C, bool LIN, int T>
-__device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
-                                         FwdSmem<C, LIN, T> &sm) {
-    using Sh = Shape<T>;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int sub = warp / Sh::KSPLIT, split = warp % Sh::KSPLIT;
-    const int sx = (sub % (T / Sh::SUB)) * Sh::SUB, sy = (sub / (T / Sh::SUB)) * Sh::SUB;
-    float D[Sh::NPX], N[C][Sh::NPX];
-    fwd_accumulate<C, LIN, T>(g, w.rec, w.pair_k + ti.start, ti.n, (float)(ti.x0 + sx),
-                              (float)(ti.y0 + sy), sm.stage[warp], D, N);
-    const int lr = lane >> 2, lc = lane & 3;
-#pragma unroll
-    for (int ry = 0; ry < Sh::RY; ++ry)
-#pragma unroll
-        for (int px = 0; px < Sh::PX; ++px) {
-            const int p = (sy + lr + 8 * ry) * T + sx + lc * Sh::PX + px;
-            const int i = ry * Sh::PX + px;
-            sm.red[split][0][p] = D[i];
-#pragma unroll
-            for (int ch = 0; ch < C; ++ch) sm.red[split][1 + ch][p] = N[ch][i];
-        }
-    __syncthreads();
-    if (Sh::KSPLIT > 1) {
-        for (int p = threadIdx.x; p < T * T; p += kThreads) {
-#pragma unroll
-            for (int v = 0; v < C + 1; ++v) {
-                float s = sm.red[0][v][p];
-#pragma unroll
-                for (int k = 1; k < Sh::KSPLIT; ++k) s += sm.red[k][v][p];
-                sm.red[0][v][p] = s;
-            }
-        }
-        __syncthreads();
-    }
+// Pixel (row, col) of the lane's pair for band slot bi, and whether this warp
+// finalises it (T = 8: only warp 0 after the reduction).
+template <int C, int T>
+__device__ __forceinline__ bool lane_pixels(int bi, int &row, int &col) {
+    using G = Geom<C, T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int band = G::KSPLIT > 1 ? 0 : warp + bi * kNW;
+    row = band * G::BROWS + lane / G::LROW;
+    col = 2 * (lane % G::LROW);
+    return G::KSPLIT == 1 || warp == 0;
 }
 
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads) k_render(const __grid_constant__ Geo g, Bufs w,
-                                                     float *__restrict__ y,
-                                                     float *__restrict__ inv_d) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(const __grid_constant__ Geo g, Bufs w,
+                                                        float *__restrict__ y,
+                                                        float *__restrict__ inv_d) {
+    using G = Geom<C, T>;
     if (status_bad(w.status)) return;
-    __shared__ __align__(16) FwdSmem<C, LIN, T> sm;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
     const TileInfo ti = tile_info(g, w, blockIdx.x);
-    fwd_tile<C, LIN, T>(g, w, ti, sm);
+    float2 Dv[G::BPW], Nv[G::BPW][C];
+    fwd_tile<C, LIN, T>(g, w, ti, sm, Dv, Nv);
     const int64_t HW = (int64_t)ti.W * ti.H;
-    for (int p = threadIdx.x; p < T * T; p += kThreads) {
-        const int xi = ti.x0 + (p % T), yi = ti.y0 + (p / T);
-        if (xi >= ti.W || yi >= ti.H) continue;
-        const float D = sm.red[0][0][p];
-        const float inv = D > 0.0f ? 1.0f / D : 0.0f;
-        const int64_t o = (int64_t)yi * ti.W + xi;
 #pragma unroll
-        for (int ch = 0; ch < C; ++ch) y[ch * HW + o] = sm.red[0][1 + ch][p] * inv;
-        if (inv_d) inv_d[o] = inv;
+    for (int bi = 0; bi < G::BPW; ++bi) {
+        int row, col;
+        if (!lane_pixels<C, T>(bi, row, col)) continue;
+        const int yi = ti.y0 + row;
+        if (yi >= ti.H) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xi = ti.x0 + col + h;
+            if (xi >= ti.W) continue;
+            const float D = h ? Dv[bi].y : Dv[bi].x;
+            const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+            const int64_t o = (int64_t)yi * ti.W + xi;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) y[ch * HW + o] = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * inv;
+            if (inv_d) inv_d[o] = inv;
+        }
     }
 }
 
 // ---------------------------------------------------------------- backward
 
-// Per-pixel upstream state: (H_0 .. H_{C-1}, Hy) with H_c = G_c / D and
-// Hy = sum_c H_c y_c; zero for pixels outside the image or with D = 0.
-template <int C>
-struct PixState {
-    static constexpr int N = C + 1 <= 2 ? 2 : 4;
+// Write the state of pixels (row, col), (row, col+1): H_c = G_c / D and
+// -Hy = -sum_c H_c y_c, as pairs {H_0a, H_0b, ..., -Hy_a, -Hy_b}.  Pixels
+// outside the image get zeros.
+template <int C, int T>
+__device__ __forceinline__ void put_state(float *pst, int row, int col, const float (&H)[2][C],
+                                          const float (&nHy)[2]) {
+    using G = Geom<C, T>;
+    float *dst = pst + row * G::RS + (col / 2) * G::PS;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+        dst[2 * ch] = H[0][ch];
+        dst[2 * ch + 1] = H[1][ch];
+    }
+    dst[2 * C] = nHy[0];
+    dst[2 * C + 1] = nHy[1];
+}
+
+// Running per-kernel sums of one lane (registers).
+template <int C, bool LIN>
+struct BwdAcc {
+    float v[Rec<C, LIN>::GS];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int q = 0; q < Rec<C, LIN>::GS; ++q) v[q] = 0.0f;
+    }
 };
 
+// Backward over the tile's list; the pixel state is in sm.pst.  `staged`:
+// the first chunk is still in shared memory from the forward.  Each lane
+// owns one kernel of the chunk (kernels with an empty row mask are dropped;
+// the rest are grouped by their first row so that a warp's 32 kernels cover
+// similar rows) and the warp walks the union of its kernels' rows together:
+// every read of pixel state is a broadcast, lanes whose kernel misses the
+// row contribute zero, and each kernel's sums stay in its lane's registers
+// until one float4 atomic per 4 sums at the end.
 template <int C, bool LIN, int T>
-__device__ __forceinline__ void bwd_accumulate(const Geo &g, const Bufs &w, const TileInfo &ti,
-                                               const float *pstate) {
+__device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
+                                         Smem<C, LIN, T> &sm, bool staged) {
     using R = Rec<C, LIN>;
-    constexpr int S = R::S, GS = R::GS;
-    constexpr int PN = PixState<C>::N;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nchunk = (ti.n + 31) >> 5;
-    for (int ci = warp; ci < nchunk; ci += kNW) {
-        const int j = ci * 32 + lane;
-        const bool valid = j < ti.n;
-        float r[S];
-        int kid = 0;
-        if (valid) {
-            kid = w.pair_k[ti.start + j];
-            const float4 *src = reinterpret_cast<const float4 *>(w.rec + (int64_t)kid * S);
-#pragma unroll
-            for (int q = 0; q < S / 4; ++q) {
-                const float4 v = __ldg(src + q);
-                r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    using G = Geom<C, T>;
+    const float qmax = g.qmax;
+    const float2 k2 = f2(kNegHalfLog2e);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float x0f = (float)ti.x0, y0f = (float)ti.y0 + 0.5f;   // exact: integers < 2^24
+    for (int c0 = 0; c0 < ti.n; c0 += G::NCH) {
+        const int nc = min(G::NCH, ti.n - c0);
+        __syncthreads();                          // previous users of the chunk are done
+        if (!(staged && c0 == 0 && ti.n <= G::NCH)) stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
+        // Group the kernels by first row (counting sort; the order inside a
+        // group does not change any kernel's sums).
+        if (threadIdx.x <= T) sm.bcnt[threadIdx.x] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            const uint32_t m = sm.mask[j];
+            if (m) atomicAdd(&sm.bcnt[__ffs(m) - 1], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < T; ++r) {
+                sm.boff[r] = acc;
+                acc += sm.bcnt[r];
+                sm.bcnt[r] = 0;
             }
-        } else {
-#pragma unroll
-            for (int q = 0; q < S; ++q) r[q] = 0.0f;
+            sm.boff[T] = acc;
         }
-        const float qm = valid ? g.qmax : -1.0f;     // inactive lanes include nothing
-        const float mx = r[0], my = r[1], a = r[2], b = r[3], c = r[4];
-        float ea[C], w0[C], w1[C];
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) {
-            ea[ch] = r[7 + ch * R::E];
-            w0[ch] = LIN ? r[7 + ch * R::E + 1] : 0.0f;
-            w1[ch] = LIN ? r[7 + ch * R::E + 2] : 0.0f;
+        __syncthreads();
+        for (int j = threadIdx.x; j < nc; j += kThreads) {
+            const uint32_t m = sm.mask[j];
+            if (m) {
+                const int r0 = __ffs(m) - 1;
+                sm.order[sm.boff[r0] + atomicAdd(&sm.bcnt[r0], 1)] = (uint8_t)j;
+            }
         }
-        float dxs[T];
+        __syncthreads();
+        const int n_live = sm.boff[T];
+        for (int grp = warp; grp * 32 < n_live; grp += kNW) {
+            const int idx = grp * 32 + lane;
+            const bool valid = idx < n_live;
+            const int j = valid ? sm.order[idx] : 0;
+            const uint32_t m = valid ? sm.mask[j] : 0u;
+            float v[R::S];
 #pragma unroll
-        for (int col = 0; col < T; ++col) dxs[col] = __fsub_rn((float)(ti.x0 + col) + 0.5f, mx);
-        float A1 = 0.f, B1 = 0.f, C1 = 0.f, A2 = 0.f, Z3 = 0.f;
-        float E[C], F[C], Fy[C];
-#pragma unroll
-        for (int ch = 0; ch < C; ++ch) { E[ch] = 0.f; F[ch] = 0.f; Fy[ch] = 0.f; }
-        for (int row = 0; row < T; ++row) {
-            const float dy = __fsub_rn((float)(ti.y0 + row) + 0.5f, my);
-            const float t = __fmul_rn(b, dy);
-            const float z1 = __fmul_rn(c, dy);
-            const float u = __fmul_rn(z1, z1);
-            float mb[C], rE[C];
+            for (int q = 0; q < R::S / 4; ++q) {
+                const float4 f = valid ? *reinterpret_cast<const float4 *>(sm.rec + j * R::SS + 4 * q)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+            }
+            const float mx = v[0], my = v[1], a = v[2], b = v[3], c = v[4];
+            float ea[C], w0[C], w1[C];
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                mb[ch] = LIN ? fmaf(w1[ch], dy, ea[ch]) : ea[ch];
-                rE[ch] = 0.f;
+                ea[ch] = v[7 + ch * R::E];
+                w0[ch] = LIN ? v[7 + ch * R::E + 1] : 0.0f;
+                w1[ch] = LIN ? v[7 + ch * R::E + 2] : 0.0f;
             }
-            float rA2 = 0.f, rS = 0.f;
-            const float *prow = pstate + row * T * PN;
+            BwdAcc<C, LIN> acc;
+            acc.zero();
+            const float2 nmx = f2(-mx), a2 = f2(a);
+            uint32_t rows = __reduce_or_sync(0xffffffffu, m);
+            while (rows) {
+                const int r = __ffs(rows) - 1;
+                rows &= rows - 1;
+                const float qm = (m >> r) & 1u ? qmax : -1.0f;   // other lanes add zero
+                const float dy = __fsub_rn(__fadd_rn(y0f, (float)r), my);
+                const float t = __fmul_rn(b, dy);
+                const float z1 = __fmul_rn(c, dy);
+                const float u = __fmul_rn(z1, z1);
+                float2 mb[C];
 #pragma unroll
-            for (int col = 0; col < T; ++col) {
-                float H[C], Hy;
-                if (PN == 4) {
-                    const float4 v = *reinterpret_cast<const float4 *>(prow + col * 4);
-                    H[0] = v.x;
-                    if (C > 1) H[1] = v.y;
-                    if (C > 2) H[2] = v.z;
-                    Hy = v.w;
-                } else {
-                    const float2 v = *reinterpret_cast<const float2 *>(prow + col * 2);
-                    H[0] = v.x;
-                    Hy = v.y;
+                for (int ch = 0; ch < C; ++ch) mb[ch] = f2(LIN ? fmaf(w1[ch], dy, ea[ch]) : ea[ch]);
+                const float2 t2 = f2(t), u2 = f2(u);
+                float2 A1 = f2(0.f), rA2 = f2(0.f), rS = f2(0.f), rE[C], F[C];
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) { rE[ch] = f2(0.f); F[ch] = f2(0.f); }
+                const float *prow = sm.pst + r * G::RS;
+                const float2 xt = f2(x0f);
+#pragma unroll
+                for (int p = 0; p < T / 2; ++p) {
+                    const float *ps = prow + p * G::PS;
+                    float2 H[C], nHy;
+                    if (C == 3) {
+                        const float4 s0 = *reinterpret_cast<const float4 *>(ps);
+                        const float4 s1 = *reinterpret_cast<const float4 *>(ps + 4);
+                        H[0] = make_float2(s0.x, s0.y);
+                        H[C > 1 ? 1 : 0] = make_float2(s0.z, s0.w);
+                        H[C > 2 ? 2 : 0] = make_float2(s1.x, s1.y);
+                        nHy = make_float2(s1.z, s1.w);
+                    } else {
+                        const float4 s0 = *reinterpret_cast<const float4 *>(ps);
+                        H[0] = make_float2(s0.x, s0.y);
+                        nHy = make_float2(s0.z, s0.w);
+                    }
+                    // pixel centres x0 + 2p + 0.5, x0 + 2p + 1.5 (exact in FP32)
+                    const float2 x2 = __fadd2_rn(xt, make_float2(2 * p + 0.5f, 2 * p + 1.5f));
+                    const float2 dx = __fadd2_rn(x2, nmx);
+                    const float2 z0 = __ffma2_rn(a2, dx, t2);
+                    const float2 q = __ffma2_rn(z0, z0, u2);
+                    const float2 arg = __fmul2_rn(q, k2);
+                    float2 e = make_float2(ex2(arg.x), ex2(arg.y));
+                    e.x = q.x <= qm ? e.x : 0.0f;
+                    e.y = q.y <= qm ? e.y : 0.0f;
+                    float2 rp = nHy;
+#pragma unroll
+                    for (int ch = 0; ch < C; ++ch) {
+                        const float2 mm = LIN ? __ffma2_rn(f2(w0[ch]), dx, mb[ch]) : mb[ch];
+                        rp = __ffma2_rn(H[ch], mm, rp);
+                    }
+                    const float2 sv = __fmul2_rn(e, rp);
+                    const float2 sz = __fmul2_rn(sv, z0);
+                    A1 = __ffma2_rn(sz, dx, A1);
+                    rA2 = __fadd2_rn(rA2, sz);
+                    rS = __fadd2_rn(rS, sv);
+                    const float2 edx = __fmul2_rn(e, dx);
+#pragma unroll
+                    for (int ch = 0; ch < C; ++ch) {
+                        rE[ch] = __ffma2_rn(e, H[ch], rE[ch]);
+                        if (LIN) F[ch] = __ffma2_rn(edx, H[ch], F[ch]);
+                    }
                 }
-                const float dx = dxs[col];
-                float z0;
-                const float q = q_of(a, dx, t, u, z0);
-                const float e = gate_e(q, qm);
-                float rp = -Hy;
+                const float a2s = rA2.x + rA2.y, ss = rS.x + rS.y;
+                acc.v[0] += A1.x + A1.y;
+                acc.v[1] = fmaf(dy, a2s, acc.v[1]);
+                acc.v[2] = fmaf(z1 * dy, ss, acc.v[2]);
+                acc.v[3] += a2s;
+                acc.v[4] = fmaf(z1, ss, acc.v[4]);
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
-                    const float m = LIN ? fmaf(w0[ch], dx, mb[ch]) : mb[ch];
-                    rp = fmaf(H[ch], m, rp);
-                }
-                const float s = e * rp;
-                const float sz = s * z0;
-                A1 = fmaf(sz, dx, A1);
-                rA2 += sz;
-                rS += s;
-                const float edx = e * dx;
-#pragma unroll
-                for (int ch = 0; ch < C; ++ch) {
-                    rE[ch] = fmaf(e, H[ch], rE[ch]);
-                    if (LIN) F[ch] = fmaf(edx, H[ch], F[ch]);
+                    const float es = rE[ch].x + rE[ch].y;
+                    acc.v[5 + ch] += es;
+                    if (LIN) {
+                        acc.v[5 + C + ch] += F[ch].x + F[ch].y;
+                        acc.v[5 + 2 * C + ch] = fmaf(dy, es, acc.v[5 + 2 * C + ch]);
+                    }
                 }
             }
-            A2 += rA2;
-            B1 = fmaf(dy, rA2, B1);
-            Z3 = fmaf(z1, rS, Z3);
-            C1 = fmaf(z1 * dy, rS, C1);
+            if (m) {
+                float4 *dst = reinterpret_cast<float4 *>(w.acc + (int64_t)sm.kid[j] * R::GS);
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) {
-                E[ch] += rE[ch];
-                if (LIN) Fy[ch] = fmaf(dy, rE[ch], Fy[ch]);
+                for (int q = 0; q < R::GS / 4; ++q)
+                    atomicAdd(dst + q, make_float4(acc.v[4 * q], acc.v[4 * q + 1], acc.v[4 * q + 2],
+                                                   acc.v[4 * q + 3]));
             }
-        }
-        if (valid) {
-            float o[GS];
-#pragma unroll
-            for (int q = 0; q < GS; ++q) o[q] = 0.f;
-            o[0] = A1; o[1] = B1; o[2] = C1; o[3] = A2; o[4] = Z3;
-#pragma unroll
-            for (int ch = 0; ch < C; ++ch) {
-                o[5 + ch] = E[ch];
-                if (LIN) { o[5 + C + ch] = F[ch]; o[5 + 2 * C + ch] = Fy[ch]; }
-            }
-            float4 *dst = reinterpret_cast<float4 *>(w.acc + (int64_t)kid * GS);
-#pragma unroll
-            for (int q = 0; q < GS / 4; ++q)
-                atomicAdd(dst + q, make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]));
         }
     }
 }
 
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads) k_render_bwd(const __grid_constant__ Geo g, Bufs w,
-                                                         const float *__restrict__ y,
-                                                         const float *__restrict__ inv_d,
-                                                         const float *__restrict__ gy,
-                                                         const float *__restrict__ target) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_bwd(const __grid_constant__ Geo g, Bufs w,
+                                                            const float *__restrict__ y,
+                                                            const float *__restrict__ inv_d,
+                                                            const float *__restrict__ gy,
+                                                            const float *__restrict__ target) {
     if (status_bad(w.status)) return;
-    constexpr int PN = PixState<C>::N;
-    __shared__ __align__(16) float pstate[T * T * PN];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
     const TileInfo ti = tile_info(g, w, blockIdx.x);
     if (ti.n == 0) return;
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float norm = 2.0f / ((float)C * (float)HW);
-    for (int p = threadIdx.x; p < T * T; p += kThreads) {
-        const int xi = ti.x0 + (p % T), yi = ti.y0 + (p / T);
-        float H[4] = {0.f, 0.f, 0.f, 0.f}, Hy = 0.f;
-        if (xi < ti.W && yi < ti.H) {
-            const int64_t o = (int64_t)yi * ti.W + xi;
-            const float inv = inv_d[o];
+    for (int pp = threadIdx.x; pp < T * T / 2; pp += kThreads) {
+        const int row = pp / (T / 2), col = 2 * (pp % (T / 2));
+        float H[2][C], nHy[2];
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) {
-                const float yv = y[ch * HW + o];
-                const float G = gy ? gy[ch * HW + o] : norm * (yv - target[ch * HW + o]);
-                H[ch] = inv * G;
-                Hy = fmaf(H[ch], yv, Hy);
+        for (int h = 0; h < 2; ++h) {
+            const int xi = ti.x0 + col + h, yi = ti.y0 + row;
+            nHy[h] = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) H[h][ch] = 0.0f;
+            if (xi < ti.W && yi < ti.H) {
+                const int64_t o = (int64_t)yi * ti.W + xi;
+                const float inv = inv_d[o];
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) {
+                    const float yv = y[ch * HW + o];
+                    const float Gv = gy ? gy[ch * HW + o] : norm * (yv - target[ch * HW + o]);
+                    H[h][ch] = inv * Gv;
+                    nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
+                }
             }
         }
-        if (PN == 4) {
-            reinterpret_cast<float4 *>(pstate)[p] = make_float4(H[0], H[1], H[2], Hy);
-        } else {
-            reinterpret_cast<float2 *>(pstate)[p] = make_float2(H[0], Hy);
-        }
+        put_state<C, T>(sm.pst, row, col, H, nHy);
     }
-    __syncthreads();
-    bwd_accumulate<C, LIN, T>(g, w, ti, pstate);
+    bwd_tile<C, LIN, T>(g, w, ti, sm, false);
 }
 
 // ---------------------------------------------------------------- fused fit tile
 
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads) k_fit_tile(const __grid_constant__ Geo g, Bufs w,
-                                                       double *loss, int32_t hist,
-                                                       const int32_t *__restrict__ step) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_fit_tile(const __grid_constant__ Geo g, Bufs w,
+                                                          double *loss, int32_t hist,
+                                                          const int32_t *__restrict__ step) {
+    using G = Geom<C, T>;
     if (status_bad(w.status)) return;
-    constexpr int PN = PixState<C>::N;
-    __shared__ __align__(16) FwdSmem<C, LIN, T> sm;
-    __shared__ __align__(16) float pstate[T * T * PN];
-    __shared__ double lsum[kNW];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
     const TileInfo ti = tile_info(g, w, blockIdx.x);
     const ImgDev &im = img_of(g, ti.b);
     const int32_t it = step ? step[ti.b] : 0;
     if (it >= im.iters) return;                      // this image has finished its run
-    fwd_tile<C, LIN, T>(g, w, ti, sm);
+    float2 Dv[G::BPW], Nv[G::BPW][C];
+    fwd_tile<C, LIN, T>(g, w, ti, sm, Dv, Nv);
     const int64_t HW = (int64_t)ti.W * ti.H;
     const float norm = 2.0f / ((float)C * (float)HW);
-    double se = 0.0;
-    for (int p = threadIdx.x; p < T * T; p += kThreads) {
-        const int xi = ti.x0 + (p % T), yi = ti.y0 + (p / T);
-        float H[4] = {0.f, 0.f, 0.f, 0.f}, Hy = 0.f;
-        if (xi < ti.W && yi < ti.H) {
-            const int64_t o = (int64_t)yi * ti.W + xi;
-            const float D = sm.red[0][0][p];
-            const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+    float se = 0.0f;                                 // this thread's <= 2 C squared errors per band
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) {
-                const float yv = sm.red[0][1 + ch][p] * inv;
-                const float d = yv - im.target[ch * HW + o];
-                se += (double)d * d;
-                H[ch] = inv * (norm * d);
-                Hy = fmaf(H[ch], yv, Hy);
+    for (int bi = 0; bi < G::BPW; ++bi) {
+        int row, col;
+        if (!lane_pixels<C, T>(bi, row, col)) continue;
+        float H[2][C], nHy[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xi = ti.x0 + col + h, yi = ti.y0 + row;
+            nHy[h] = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) H[h][ch] = 0.0f;
+            if (xi < ti.W && yi < ti.H) {
+                const int64_t o = (int64_t)yi * ti.W + xi;
+                const float D = h ? Dv[bi].y : Dv[bi].x;
+                const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) {
+                    const float yv = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * inv;
+                    const float d = yv - im.target[ch * HW + o];
+                    se = fmaf(d, d, se);
+                    H[h][ch] = inv * (norm * d);
+                    nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
+                }
             }
         }
-        if (PN == 4) {
-            reinterpret_cast<float4 *>(pstate)[p] = make_float4(H[0], H[1], H[2], Hy);
-        } else {
-            reinterpret_cast<float2 *>(pstate)[p] = make_float2(H[0], Hy);
-        }
+        put_state<C, T>(sm.pst, row, col, H, nHy);
     }
     if (loss) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-        if ((threadIdx.x & 31) == 0) lsum[threadIdx.x >> 5] = se;
+        if ((threadIdx.x & 31) == 0) sm.lsum[threadIdx.x >> 5] = (double)se;
     }
     __syncthreads();
     if (loss && threadIdx.x == 0 && it < hist) {
         double s = 0.0;
-        for (int i = 0; i < kNW; ++i) s += lsum[i];
+        for (int i = 0; i < kNW; ++i) s += sm.lsum[i];
         atomicAdd(loss + (int64_t)ti.b * hist + it, s / ((double)C * (double)HW));
     }
     if (ti.n == 0) return;
-    bwd_accumulate<C, LIN, T>(g, w, ti, pstate);
+    bwd_tile<C, LIN, T>(g, w, ti, sm, true);
 }
 
 // ---------------------------------------------------------------- finalize
@@ -488,25 +658,54 @@ __global__ void k_finalize(const __grid_constant__ Geo g, Bufs w, smoe_params gr
     grad.chol[3 * k + 2] += -s[2] / g.scale;
 }
 
+// Raise a tile kernel's dynamic shared-memory limit once per instantiation.
+template <typename K>
+cudaError_t smem_attr(K kern, size_t smem, bool &done) {
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int C, bool LIN, int T>
+cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y, float *yo,
+                         float *inv_do, const float *inv_d, const float *gy, const float *target,
+                         double *loss, int32_t hist, const int32_t *step, cudaStream_t st) {
+    const unsigned grid = (unsigned)g.tiles_total;
+    if (grid == 0) return cudaSuccess;
+    constexpr size_t smem = smem_bytes<C, LIN, T>();
+    static bool a0 = false, a1 = false, a2 = false;
+    cudaError_t e;
+    if (which == 0) {
+        if ((e = smem_attr(k_render<C, LIN, T>, smem, a0)) != cudaSuccess) return e;
+        k_render<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, yo, inv_do);
+    } else if (which == 1) {
+        if ((e = smem_attr(k_render_bwd<C, LIN, T>, smem, a1)) != cudaSuccess) return e;
+        k_render_bwd<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, y, inv_d, gy, target);
+    } else {
+        if ((e = smem_attr(k_fit_tile<C, LIN, T>, smem, a2)) != cudaSuccess) return e;
+        k_fit_tile<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, loss, hist, step);
+    }
+    return cudaGetLastError();
+}
+
 template <int C, bool LIN>
 cudaError_t dispatch_T(const Geo &g, const Bufs &w, int which, const float *y, float *yo,
                        float *inv_do, const float *inv_d, const float *gy, const float *target,
                        double *loss, int32_t hist, const int32_t *step, cudaStream_t st) {
-    const unsigned grid = (unsigned)g.tiles_total;
-    if (grid == 0) return cudaSuccess;
-#define SMOE_LAUNCH(TT)                                                                   \
-    if (which == 0) k_render<C, LIN, TT><<<grid, kThreads, 0, st>>>(g, w, yo, inv_do);    \
-    else if (which == 1)                                                                  \
-        k_render_bwd<C, LIN, TT><<<grid, kThreads, 0, st>>>(g, w, y, inv_d, gy, target);  \
-    else k_fit_tile<C, LIN, TT><<<grid, kThreads, 0, st>>>(g, w, loss, hist, step);
     switch (g.T) {
-        case 8: SMOE_LAUNCH(8) break;
-        case 16: SMOE_LAUNCH(16) break;
-        case 32: SMOE_LAUNCH(32) break;
+        case 8:
+            return dispatch_one<C, LIN, 8>(g, w, which, y, yo, inv_do, inv_d, gy, target, loss,
+                                           hist, step, st);
+        case 16:
+            return dispatch_one<C, LIN, 16>(g, w, which, y, yo, inv_do, inv_d, gy, target, loss,
+                                            hist, step, st);
+        case 32:
+            return dispatch_one<C, LIN, 32>(g, w, which, y, yo, inv_do, inv_d, gy, target, loss,
+                                            hist, step, st);
         default: return cudaErrorInvalidValue;
     }
-#undef SMOE_LAUNCH
-    return cudaGetLastError();
 }
 
 cudaError_t dispatch(const Geo &g, const Bufs &w, int which, const float *y, float *yo,
