@@ -164,9 +164,9 @@ SMOE_API smoe_status smoe_sq_error(const float *y, const float *target, int64_t 
 
 typedef struct {
     int32_t W, H;           /* image size */
-    int64_t K;              /* kernels of this image */
-    int64_t k_off;          /* first kernel of this image in the batch's SoA arrays */
     const float *target;    /* C x H x W (device) */
+    smoe_params p;          /* this image's parameters (device SoA, K = p.K), updated in place */
+    smoe_params m, v;       /* its Adam moments (device SoA, same K) */
     int32_t iters;          /* length of this image's run (lr schedule, loss history) */
     float lr_mu0, lr_mu1;   /* centre rate, decayed exponentially lr_mu0 -> lr_mu1 */
     float lr_chol, lr_ea, lr_eW;
@@ -177,17 +177,22 @@ typedef struct {
     int32_t C, tile, expert;
     float qmax;
     double b1, b2, eps;     /* Adam (1 - b and the bias corrections are formed in FP64) */
-    smoe_params p, m, v;    /* batch SoA (device): K_total kernels, image b at k_off */
     int32_t *step;          /* device, B: iterations done per image (caller-owned) */
     double *loss;           /* device, B x hist: MSE per image and iteration, or NULL */
     int32_t hist;           /* columns of `loss` */
+    int32_t persistent;     /* 1: the fused tile kernel runs as one persistent grid that
+                               takes tiles from a work queue; 0: one CTA per tile */
 } smoe_fit_batch;
 
 /* Workspace bytes for a fit of this batch with pair_cap pairs in total. */
 SMOE_API smoe_status smoe_fit_workspace_size(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
                                     int64_t pair_cap, size_t *bytes);
 
-/* Prepare a fit: writes the batch table into `ws` (one host-to-device copy
+/* Images keep their own parameter tensors, so a batch can be re-formed (an
+ * image added or retired) without moving any parameters: build the new
+ * batch and call smoe_fit_init with reset = 0 to continue the others' runs.
+ *
+ * Prepare a fit: writes the batch table into `ws` (one host-to-device copy
  * on `stream`, after which the stream is synchronised once) and zeroes the
  * workspace's gradient sums.  With reset != 0 it also zeroes the Adam moments
  * m and v, the step counters, the loss history and the status word, i.e.

@@ -35,8 +35,8 @@ class Params(ctypes.Structure):
 
 
 class FitImage(ctypes.Structure):
-    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("K", ctypes.c_int64),
-                ("k_off", ctypes.c_int64), ("target", ctypes.c_void_p),
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("target", ctypes.c_void_p),
+                ("p", Params), ("m", Params), ("v", Params),
                 ("iters", ctypes.c_int32), ("lr_mu0", ctypes.c_float),
                 ("lr_mu1", ctypes.c_float), ("lr_chol", ctypes.c_float),
                 ("lr_ea", ctypes.c_float), ("lr_eW", ctypes.c_float)]
@@ -45,9 +45,9 @@ class FitImage(ctypes.Structure):
 class FitBatch(ctypes.Structure):
     _fields_ = [("B", ctypes.c_int32), ("C", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("expert", ctypes.c_int32), ("qmax", ctypes.c_float), ("b1", ctypes.c_double),
-                ("b2", ctypes.c_double), ("eps", ctypes.c_double), ("p", Params),
-                ("m", Params), ("v", Params), ("step", ctypes.c_void_p),
-                ("loss", ctypes.c_void_p), ("hist", ctypes.c_int32)]
+                ("b2", ctypes.c_double), ("eps", ctypes.c_double), ("step", ctypes.c_void_p),
+                ("loss", ctypes.c_void_p), ("hist", ctypes.c_int32),
+                ("persistent", ctypes.c_int32)]
 
 
 _lib = None

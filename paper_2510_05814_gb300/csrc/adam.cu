@@ -82,11 +82,8 @@ __global__ void k_adam_coefs(const __grid_constant__ Geo g, const int32_t *step,
 // (+ 2C) parameters of the kernel; zeroes the sums.  The last CTA to finish
 // advances every running image's step counter and forms the coefficients of
 // the next step.
-__global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, float *chol,
-                           float *ea, float *eW, float *m_mu, float *m_chol, float *m_ea,
-                           float *m_eW, float *v_mu, float *v_chol, float *v_ea, float *v_eW,
-                           double b1, double b2, Betas be, int32_t *step, uint32_t *done,
-                           float *coef) {
+__global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2,
+                           Betas be, int32_t *step, uint32_t *done, float *coef) {
     if (status_bad(w.status)) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < g.K_total) {
@@ -94,6 +91,10 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, flo
         const ImgDev &im = img_of(g, b);
         const int32_t it = step[b];
         if (it < im.iters) {
+            const int64_t kl = k - im.k_off;
+            float *mu = im.p.mu, *chol = im.p.chol, *ea = im.p.ea, *eW = im.p.eW;
+            float *m_mu = im.m.mu, *m_chol = im.m.chol, *m_ea = im.m.ea, *m_eW = im.m.eW;
+            float *v_mu = im.v.mu, *v_chol = im.v.chol, *v_ea = im.v.ea, *v_eW = im.v.eW;
             // A kernel listed in no tile touched no pixel: its gradient is 0
             // (and must not become inf * 0 for non-finite parameters).
             const int4 rc = w.rect[k];
@@ -112,7 +113,7 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, flo
             float gmx = 0.f, gmy = 0.f;
             if (rc.x <= rc.z) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
             for (int ch = 0; ch < C; ++ch) {
-                const int64_t x = k * C + ch;
+                const int64_t x = kl * C + ch;
                 float pv = ea[x], mv = m_ea[x], vv = v_ea[x];
                 adam1(pv, s[5 + ch], mv, vv, kea);
                 ea[x] = pv; m_ea[x] = mv; v_ea[x] = vv;
@@ -131,14 +132,14 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, float *mu, flo
             }
             const float gm[2] = {gmx * (float)im.W, gmy * (float)im.H};
             for (int d = 0; d < 2; ++d) {
-                float pv = mu[2 * k + d], mv = m_mu[2 * k + d], vv = v_mu[2 * k + d];
+                float pv = mu[2 * kl + d], mv = m_mu[2 * kl + d], vv = v_mu[2 * kl + d];
                 adam1(pv, gm[d], mv, vv, kmu);
-                mu[2 * k + d] = pv; m_mu[2 * k + d] = mv; v_mu[2 * k + d] = vv;
+                mu[2 * kl + d] = pv; m_mu[2 * kl + d] = mv; v_mu[2 * kl + d] = vv;
             }
             for (int d = 0; d < 3; ++d) {
-                float pv = chol[3 * k + d], mv = m_chol[3 * k + d], vv = v_chol[3 * k + d];
+                float pv = chol[3 * kl + d], mv = m_chol[3 * kl + d], vv = v_chol[3 * kl + d];
                 adam1(pv, -s[d], mv, vv, kch);
-                chol[3 * k + d] = pv; m_chol[3 * k + d] = mv; v_chol[3 * k + d] = vv;
+                chol[3 * kl + d] = pv; m_chol[3 * kl + d] = mv; v_chol[3 * kl + d] = vv;
             }
             for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
         }
@@ -201,16 +202,12 @@ cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const s
     return cudaGetLastError();
 }
 
-cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
-                            float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
-                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, double b1,
-                            double b2, double eps, int32_t *step, uint32_t *done, float *coef,
-                            cudaStream_t st) {
+cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, double eps,
+                            int32_t *step, uint32_t *done, float *coef, cudaStream_t st) {
     const unsigned blocks = (unsigned)((g.K_total + 255) / 256);
     if (blocks == 0) return cudaSuccess;
     const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
-    k_fit_adam<<<blocks, 256, 0, st>>>(g, w, mu, chol, ea, eW, m_mu, m_chol, m_ea, m_eW, v_mu,
-                                       v_chol, v_ea, v_eW, b1, b2, be, step, done, coef);
+    k_fit_adam<<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
     return cudaGetLastError();
 }
 

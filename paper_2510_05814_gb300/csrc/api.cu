@@ -24,7 +24,7 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 // Workspace regions, in order; `fit` adds the batch table and the lists.
 struct Layout {
     size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
-    size_t table, tile_off, pair_k, n_pairs, done, coef;
+    size_t table, tile_off, pair_k, n_pairs, done, work, coef;
     size_t total;
 };
 
@@ -47,6 +47,7 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
         L.pair_k = take(sizeof(int32_t) * (size_t)pair_cap);
         L.n_pairs = take(sizeof(int64_t));
         L.done = take(sizeof(uint32_t));
+        L.work = take(sizeof(uint32_t));
         L.coef = take(sizeof(float) * 8 * (size_t)B);
     }
     L.total = o;
@@ -94,6 +95,7 @@ Geo make_geo(const smoe_desc *d, int64_t K) {
     g.one.k_off = 0;
     g.one.t_off = 0;
     g.one.iters = 1;
+    g.one.p.K = K;
     return g;
 }
 
@@ -127,22 +129,29 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
     if (bt->expert != 0 && bt->expert != 1) return false;
     if (!(bt->qmax > 0.0f) || !bt->step) return false;
     if (bt->loss && bt->hist <= 0) return false;
-    const smoe_params *ps[3] = {&bt->p, &bt->m, &bt->v};
     int64_t K_total = 0, t_total = 0;
     tab->resize(bt->B);
     for (int b = 0; b < bt->B; ++b) {
         const smoe_fit_image &im = imgs[b];
-        if (im.W <= 0 || im.H <= 0 || im.K < 0 || !im.target || im.iters < 0) return false;
-        if (im.k_off != K_total) return false;            // images packed in order
+        if (im.W <= 0 || im.H <= 0 || im.p.K < 0 || !im.target || im.iters < 0) return false;
+        const smoe_params *ps[3] = {&im.p, &im.m, &im.v};
+        for (const smoe_params *q : ps) {
+            if (q->K != im.p.K) return false;
+            if (q->K > 0 && (!q->mu || !q->chol || !q->ea)) return false;
+            if (q->K > 0 && ((q->eW != nullptr) != (bt->expert == 1))) return false;
+        }
         ImgDev &d = (*tab)[b];
         d.W = im.W;
         d.H = im.H;
         d.tiles_x = (im.W + bt->tile - 1) / bt->tile;
         d.tiles_y = (im.H + bt->tile - 1) / bt->tile;
-        d.K = im.K;
-        d.k_off = im.k_off;
+        d.K = im.p.K;
+        d.k_off = K_total;
         d.t_off = t_total;
         d.target = im.target;
+        d.p = im.p;
+        d.m = im.m;
+        d.v = im.v;
         d.iters = im.iters;
         d.lr_mu0 = im.lr_mu0;
         d.lr_mu1 = im.lr_mu1 > 0.0f ? im.lr_mu1 : im.lr_mu0;
@@ -150,15 +159,10 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
         d.lr_ea = im.lr_ea;
         d.lr_eW = im.lr_eW;
         if (!(d.lr_mu0 > 0.0f)) d.lr_mu0 = d.lr_mu1 = 0.0f;
-        K_total += im.K;
+        K_total += im.p.K;
         t_total += (int64_t)d.tiles_x * d.tiles_y;
     }
     if (K_total > 0x7fffffffLL || t_total > kMaxTiles) return false;
-    for (const smoe_params *p : ps) {
-        if (p->K != K_total) return false;
-        if (K_total > 0 && (!p->mu || !p->chol || !p->ea)) return false;
-        if (K_total > 0 && ((p->eW != nullptr) != (bt->expert == 1))) return false;
-    }
     Geo &G = *g;
     G = Geo{};
     G.C = bt->C;
@@ -171,10 +175,6 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
     G.B = bt->B;
     G.K_total = K_total;
     G.tiles_total = t_total;
-    G.mu = bt->p.mu;
-    G.chol = bt->p.chol;
-    G.ea = bt->p.ea;
-    G.eW = bt->p.eW;
     if (bt->B == 1) {
         G.table = nullptr;
         G.one = (*tab)[0];
@@ -207,10 +207,7 @@ smoe_status smoe_bin(const smoe_desc *d, const smoe_params *p, void *ws, size_t 
     Geo g = make_geo(d, p->K);
     const Layout L = layout(p->K, g.tiles_total, pair_cap, g.S, g.GS, 1, false);
     if (!ws_ok(ws, ws_bytes, L.total)) return SMOE_ERR_WORKSPACE;
-    g.mu = p->mu;
-    g.chol = p->chol;
-    g.ea = p->ea;
-    g.eW = p->eW;
+    g.one.p = *p;
     Bufs w = make_bufs(ws, L);
     w.tile_off = tile_off;
     w.pair_k = pair_k;
@@ -248,10 +245,7 @@ smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params *p, void 
     // pair_cap = 0 gives the offsets whatever pair_cap the workspace was made for.
     const Layout L = layout(p->K, g.tiles_total, 0, g.S, g.GS, 1, false);
     if (!ws_ok(ws, ws_bytes, L.total)) return SMOE_ERR_WORKSPACE;
-    g.mu = p->mu;
-    g.chol = p->chol;
-    g.ea = p->ea;
-    g.eW = p->eW;
+    g.one.p = *p;
     Bufs w = make_bufs(ws, L);
     w.tile_off = const_cast<int32_t *>(tile_off);
     w.pair_k = const_cast<int32_t *>(pair_k);
@@ -304,6 +298,7 @@ static smoe_status fit_bufs(const smoe_fit_batch *batch, const smoe_fit_image *i
     w->tile_off = reinterpret_cast<int32_t *>(b + L->tile_off);
     w->pair_k = reinterpret_cast<int32_t *>(b + L->pair_k);
     w->n_pairs = reinterpret_cast<int64_t *>(b + L->n_pairs);
+    w->work = reinterpret_cast<uint32_t *>(b + L->work);
     w->pair_cap = pair_cap;
     w->status = status;
     return SMOE_OK;
@@ -325,15 +320,17 @@ smoe_status smoe_fit_init(const smoe_fit_batch *batch, const smoe_fit_image *img
     if (e == cudaSuccess) e = cudaMemsetAsync(w.acc, 0, sizeof(float) * g.GS * g.K_total, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b + L.done, 0, sizeof(uint32_t), st);
     if (reset && e == cudaSuccess) {
-        const smoe_params *mv[2] = {&batch->m, &batch->v};
-        const int64_t K = g.K_total;
-        for (const smoe_params *x : mv) {
-            if (K == 0) break;
-            if (e == cudaSuccess) e = cudaMemsetAsync(x->mu, 0, sizeof(float) * 2 * K, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(x->chol, 0, sizeof(float) * 3 * K, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(x->ea, 0, sizeof(float) * g.C * K, st);
-            if (e == cudaSuccess && x->eW)
-                e = cudaMemsetAsync(x->eW, 0, sizeof(float) * 2 * g.C * K, st);
+        for (int bi = 0; bi < batch->B && e == cudaSuccess; ++bi) {
+            const smoe_params *mv[2] = {&imgs[bi].m, &imgs[bi].v};
+            const int64_t K = imgs[bi].p.K;
+            for (const smoe_params *x : mv) {
+                if (K == 0) break;
+                if (e == cudaSuccess) e = cudaMemsetAsync(x->mu, 0, sizeof(float) * 2 * K, st);
+                if (e == cudaSuccess) e = cudaMemsetAsync(x->chol, 0, sizeof(float) * 3 * K, st);
+                if (e == cudaSuccess) e = cudaMemsetAsync(x->ea, 0, sizeof(float) * g.C * K, st);
+                if (e == cudaSuccess && x->eW)
+                    e = cudaMemsetAsync(x->eW, 0, sizeof(float) * 2 * g.C * K, st);
+            }
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(batch->step, 0, sizeof(int32_t) * g.B, st);
         if (e == cudaSuccess && batch->loss)
@@ -351,14 +348,14 @@ smoe_status smoe_fit_init(const smoe_fit_batch *batch, const smoe_fit_image *img
 
 static cudaError_t fit_phase(const smoe_fit_batch *batch, const Geo &g, const Bufs &w,
                              uint32_t *done, float *coef, int phase, cudaStream_t st) {
-    const smoe_params &p = batch->p, &m = batch->m, &v = batch->v;
     switch (phase) {
         case 0: return launch_bin(g, w, st);
-        case 1: return launch_fit_tiles(g, w, batch->loss, batch->hist, batch->step, st);
+        case 1:
+            return launch_fit_tiles(g, w, batch->loss, batch->hist, batch->step,
+                                    batch->persistent != 0, st);
         case 2:
-            return launch_fit_adam(g, w, p.mu, p.chol, p.ea, p.eW, m.mu, m.chol, m.ea, m.eW,
-                                   v.mu, v.chol, v.ea, v.eW, batch->b1, batch->b2, batch->eps,
-                                   batch->step, done, coef, st);
+            return launch_fit_adam(g, w, batch->b1, batch->b2, batch->eps, batch->step, done,
+                                   coef, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -74,10 +74,11 @@ __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
     const bool valid = k_raw < g.K_total;
     const int64_t k = valid ? k_raw : g.K_total - 1;   // inactive lanes mirror the last kernel
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
+    const int64_t kl = k - im.k_off;                   // the image's own kernel index
     // Kernel in output-pixel units, one rounding per operation.
-    float mx = __fmul_rn(g.mu[2 * k], (float)im.W);
-    float my = __fmul_rn(g.mu[2 * k + 1], (float)im.H);
-    float a = g.chol[3 * k], b = g.chol[3 * k + 1], c = g.chol[3 * k + 2];
+    float mx = __fmul_rn(im.p.mu[2 * kl], (float)im.W);
+    float my = __fmul_rn(im.p.mu[2 * kl + 1], (float)im.H);
+    float a = im.p.chol[3 * kl], b = im.p.chol[3 * kl + 1], c = im.p.chol[3 * kl + 2];
     const bool scaled = g.scale != 1.0f;
     if (scaled) {
         a = __fdiv_rn(a, g.scale);
@@ -89,9 +90,9 @@ __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
         r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c; r[5] = 0.0f; r[6] = 0.0f;
         const int E = g.linear ? 3 : 1;
         for (int ch = 0; ch < g.C; ++ch) {
-            r[7 + ch * E] = g.ea[k * g.C + ch];
+            r[7 + ch * E] = im.p.ea[kl * g.C + ch];
             if (g.linear) {
-                float w0 = g.eW[(k * g.C + ch) * 2], w1 = g.eW[(k * g.C + ch) * 2 + 1];
+                float w0 = im.p.eW[(kl * g.C + ch) * 2], w1 = im.p.eW[(kl * g.C + ch) * 2 + 1];
                 if (scaled) { w0 = __fdiv_rn(w0, g.scale); w1 = __fdiv_rn(w1, g.scale); }
                 r[7 + ch * E + 1] = w0;
                 r[7 + ch * E + 2] = w1;

@@ -88,6 +88,7 @@ struct Smem {
     uint8_t order[G::NCH];               // backward: kernels grouped by first row
     int bcnt[T + 1], boff[T + 1];
     double lsum[kNW];
+    long long next;                      // persistent launch: the CTA's next tile
 };
 
 template <int C, bool LIN, int T>
@@ -569,15 +570,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_bwd(const __gri
 
 // ---------------------------------------------------------------- fused fit tile
 
+// Forward, MSE and backward of global tile t (all threads of the CTA).
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_fit_tile(const __grid_constant__ Geo g, Bufs w,
-                                                          double *loss, int32_t hist,
-                                                          const int32_t *__restrict__ step) {
+__device__ __forceinline__ void fit_tile_body(const Geo &g, const Bufs &w, int64_t t,
+                                              Smem<C, LIN, T> &sm, double *loss, int32_t hist,
+                                              const int32_t *__restrict__ step) {
     using G = Geom<C, T>;
-    if (status_bad(w.status)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
-    const TileInfo ti = tile_info(g, w, blockIdx.x);
+    const TileInfo ti = tile_info(g, w, t);
     const ImgDev &im = img_of(g, ti.b);
     const int32_t it = step ? step[ti.b] : 0;
     if (it >= im.iters) return;                      // this image has finished its run
@@ -626,6 +625,35 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_fit_tile(const __grid_
     }
     if (ti.n == 0) return;
     bwd_tile<C, LIN, T>(g, w, ti, sm, true);
+}
+
+template <int C, bool LIN, int T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_fit_tile(const __grid_constant__ Geo g, Bufs w,
+                                                          double *loss, int32_t hist,
+                                                          const int32_t *__restrict__ step) {
+    if (status_bad(w.status)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
+    fit_tile_body<C, LIN, T>(g, w, blockIdx.x, sm, loss, hist, step);
+}
+
+// The same work as one persistent grid: each CTA takes the next tile from a
+// queue (a counter zeroed before the launch) until the table is exhausted.
+template <int C, bool LIN, int T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_fit_tile_persistent(const __grid_constant__ Geo g, Bufs w, double *loss, int32_t hist,
+                          const int32_t *__restrict__ step) {
+    if (status_bad(w.status)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
+    for (;;) {
+        if (threadIdx.x == 0) sm.next = (long long)atomicAdd(w.work, 1u);
+        __syncthreads();
+        const int64_t t = sm.next;
+        __syncthreads();
+        if (t >= g.tiles_total) break;
+        fit_tile_body<C, LIN, T>(g, w, t, sm, loss, hist, step);
+    }
 }
 
 // ---------------------------------------------------------------- finalize
@@ -683,9 +711,26 @@ cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y,
     } else if (which == 1) {
         if ((e = smem_attr(k_render_bwd<C, LIN, T>, smem, a1)) != cudaSuccess) return e;
         k_render_bwd<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, y, inv_d, gy, target);
-    } else {
+    } else if (which == 2) {
         if ((e = smem_attr(k_fit_tile<C, LIN, T>, smem, a2)) != cudaSuccess) return e;
         k_fit_tile<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, loss, hist, step);
+    } else {
+        static bool a3 = false;
+        static int resident = 0;
+        if ((e = smem_attr(k_fit_tile_persistent<C, LIN, T>, smem, a3)) != cudaSuccess) return e;
+        if (!resident) {
+            int dev = 0, sms = 0, per_sm = 0;
+            if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return e;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                     &per_sm, k_fit_tile_persistent<C, LIN, T>, kThreads, smem)) != cudaSuccess)
+                return e;
+            resident = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        if ((e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        const unsigned pg = grid < (unsigned)resident ? grid : (unsigned)resident;
+        k_fit_tile_persistent<C, LIN, T><<<pg, kThreads, smem, st>>>(g, w, loss, hist, step);
     }
     return cudaGetLastError();
 }
@@ -741,9 +786,9 @@ cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const
 }
 
 cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,
-                             const int32_t *step, cudaStream_t st) {
-    return dispatch(g, w, 2, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, loss, hist,
-                    step, st);
+                             const int32_t *step, bool persistent, cudaStream_t st) {
+    return dispatch(g, w, persistent ? 3 : 2, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, loss, hist, step, st);
 }
 
 }  // namespace smoe

@@ -26,10 +26,14 @@ namespace smoe {
 constexpr int kMaxC = 3;
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
 
+// One image of a launch.  Its kernels have global ids [k_off, k_off + K) and
+// its tiles [t_off, t_off + tiles_x * tiles_y); p / m / v are the image's own
+// SoA parameters and Adam moments (local kernel ids).
 struct ImgDev {
     int32_t W, H, tiles_x, tiles_y;
     int64_t K, k_off, t_off;
     const float *target;
+    smoe_params p, m, v;
     int32_t iters;
     float lr_mu0, lr_mu1, lr_chol, lr_ea, lr_eW;
 };
@@ -41,8 +45,6 @@ struct Geo {
     int64_t K_total, tiles_total;
     const ImgDev *table;   // device array of B entries, or nullptr (then `one`)
     ImgDev one;
-    // user SoA parameters of all kernels of the launch (global kernel ids)
-    const float *mu, *chol, *ea, *eW;
 };
 
 struct Bufs {
@@ -60,6 +62,7 @@ struct Bufs {
     int64_t *n_pairs;
     int64_t pair_cap;
     int32_t *status;
+    uint32_t *work;      // tile queue of the persistent fit launch (fit only)
 };
 
 __host__ __device__ inline int rec_stride(int C, int linear) {
@@ -129,15 +132,12 @@ cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const
                               const float *gy, const float *target, const smoe_params &grad,
                               cudaStream_t st);
 cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,
-                             const int32_t *step, cudaStream_t st);
+                             const int32_t *step, bool persistent, cudaStream_t st);
 cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
                             const smoe_params &v, int C, const float lr[4], double b1, double b2,
                             double eps, int32_t step, cudaStream_t st);
-cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, float *mu, float *chol, float *ea,
-                            float *eW, float *m_mu, float *m_chol, float *m_ea, float *m_eW,
-                            float *v_mu, float *v_chol, float *v_ea, float *v_eW, double b1,
-                            double b2, double eps, int32_t *step, uint32_t *done, float *coef,
-                            cudaStream_t st);
+cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, double eps,
+                            int32_t *step, uint32_t *done, float *coef, cudaStream_t st);
 cudaError_t launch_adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
                               float *coef, cudaStream_t st);
 cudaError_t launch_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out,

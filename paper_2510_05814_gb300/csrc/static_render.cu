@@ -104,10 +104,7 @@ extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smo
     g.one.tiles_y = tiles_y;
     g.one.K = p->K;
     g.one.iters = 1;
-    g.mu = p->mu;
-    g.chol = p->chol;
-    g.ea = p->ea;
-    g.eW = p->eW;
+    g.one.p = *p;
 
     Bufs w{};
     w.rec = reinterpret_cast<float *>(b + kRec);

@@ -19,12 +19,13 @@ class FitBatch:
     """B images fitted together.
 
     targets: list of (C,H,W) float32 CUDA tensors; params: list of SMoEParams
-    (initial values, copied into one batch SoA); iters: per-image run length
-    (int or list); lr = (mu0, mu1, chol, ea, eW)."""
+    (each image's own tensors, updated in place); iters: per-image run length
+    (int or list); lr = (mu0, mu1, chol, ea, eW) or one tuple per image;
+    persistent: run the fused tile kernel as one persistent grid."""
 
     def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
                  qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
-                 device="cuda"):
+                 persistent=False, pair_cap=None, device="cuda"):
         assert len(targets) == len(params) and len(targets) > 0
         self.B = len(targets)
         self.device = device
@@ -32,30 +33,29 @@ class FitBatch:
         self.linear = params[0].linear
         self.tile, self.qmax = tile, qmax
         self.b1, self.b2, self.eps = b1, b2, eps
+        self.persistent = bool(persistent)
         self.targets = [t.contiguous() for t in targets]
         self.iters = [iters] * self.B if np.isscalar(iters) else list(iters)
         self.lr = [lr] * self.B if np.isscalar(lr[0]) else list(lr)
+        self.params = list(params)
         self.Ks = [p.K for p in params]
-        self.k_off = np.concatenate([[0], np.cumsum(self.Ks)]).astype(np.int64)
-        cat = lambda xs: torch.cat([x for x in xs], 0).contiguous()
-        self.p = SMoEParams(cat([p.mu for p in params]), cat([p.chol for p in params]),
-                            cat([p.ea for p in params]),
-                            cat([p.eW for p in params]) if self.linear else None)
-        self.m = self.p.zeros_like()
-        self.v = self.p.zeros_like()
+        self.m = [p.zeros_like() for p in params]
+        self.v = [p.zeros_like() for p in params]
         self.step = torch.zeros(self.B, dtype=torch.int32, device=device)
         self.hist = int(hist if hist is not None else max(self.iters))
         self.loss = torch.zeros(self.B, max(self.hist, 1), dtype=torch.float64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.graph = None
-        # Pair capacity: bin each image once with its initial parameters.
-        total = 0
-        for b in range(self.B):
-            t = self.targets[b]
-            desc = RasterDesc(t.shape[2], t.shape[1], self.C, tile, self.linear, qmax, 1.0)
-            r = Rasterizer(desc, self.Ks[b]).bin(self.params_of(b))
-            total += int(r.n_pairs.item())
-        self.pair_cap = int(total * pair_slack) + 4096
+        if pair_cap is None:
+            # Pair capacity: bin each image once with its initial parameters.
+            total = 0
+            for b in range(self.B):
+                t = self.targets[b]
+                desc = RasterDesc(t.shape[2], t.shape[1], self.C, tile, self.linear, qmax, 1.0)
+                r = Rasterizer(desc, self.Ks[b]).bin(self.params[b])
+                total += int(r.n_pairs.item())
+            pair_cap = int(total * pair_slack) + 4096
+        self.pair_cap = int(pair_cap)
         self._setup(reset=True)
 
     # -- C structs
@@ -64,12 +64,12 @@ class FitBatch:
         for b in range(self.B):
             t = self.targets[b]
             lr = self.lr[b]
-            imgs[b] = _lib.FitImage(t.shape[2], t.shape[1], self.Ks[b], int(self.k_off[b]),
-                                    _ptr(t), int(self.iters[b]), lr[0], lr[1], lr[2], lr[3],
-                                    lr[4])
+            imgs[b] = _lib.FitImage(t.shape[2], t.shape[1], _ptr(t), self.params[b].c(),
+                                    self.m[b].c(), self.v[b].c(), int(self.iters[b]), lr[0],
+                                    lr[1], lr[2], lr[3], lr[4])
         batch = _lib.FitBatch(self.B, self.C, self.tile, int(self.linear), self.qmax, self.b1,
-                              self.b2, self.eps, self.p.c(), self.m.c(), self.v.c(),
-                              _ptr(self.step), _ptr(self.loss), self.hist)
+                              self.b2, self.eps, _ptr(self.step), _ptr(self.loss), self.hist,
+                              int(self.persistent))
         return batch, imgs
 
     def _setup(self, reset):
@@ -89,13 +89,7 @@ class FitBatch:
         self.graph = None
 
     def params_of(self, b):
-        s, e = int(self.k_off[b]), int(self.k_off[b + 1])
-        return SMoEParams(self.p.mu[s:e], self.p.chol[s:e], self.p.ea[s:e],
-                          None if self.eW is None else self.eW[s:e])
-
-    @property
-    def eW(self):
-        return self.p.eW
+        return self.params[b]
 
     def launch(self, n_iters=1, stream=None):
         """Enqueue n_iters iterations (no host synchronisation)."""

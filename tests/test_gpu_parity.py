@@ -273,7 +273,7 @@ def test_fit_matches_oracle_trajectory():
     fb.run(8)
     got = fb.losses()[0]
     np.testing.assert_allclose(got, ref_loss, rtol=1e-4)
-    np.testing.assert_allclose(fb.p.mu.cpu().numpy(), m.mu, rtol=0, atol=2e-5)
+    np.testing.assert_allclose(fb.params_of(0).mu.cpu().numpy(), m.mu, rtol=0, atol=2e-5)
 
 
 def test_batched_fit_equals_single_image_fits():
@@ -303,3 +303,21 @@ def test_graph_replay_equals_eager():
     b = FitBatch([tt], [p.clone()], 12, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2)).run(12, graph_iters=4)
     np.testing.assert_allclose(a.losses(), b.losses(), rtol=1e-5)
     assert int(b.step.item()) == 12
+
+
+def test_persistent_launch_equals_grid_launch():
+    """The persistent fused tile kernel (work queue) gives the grid launch's
+    results on a ragged batch."""
+    sizes = [(70, 50), (33, 90), (128, 40)]
+    ts, ps = [], []
+    for i, (W, H) in enumerate(sizes):
+        t = synth.polygon_image(W, H, 3, 5, 90 + i)
+        ts.append(torch.tensor(t, device="cuda"))
+        ps.append(api.SMoEParams.from_numpy(synth.init_params(t, (W * H) // 16, 3.0, True, 90 + i)))
+    lr = (1e-2, 1e-3, 1e-2, 1e-2, 1e-2)
+    a = FitBatch(ts, [p.clone() for p in ps], 5, lr=lr, persistent=False).run(5)
+    b = FitBatch(ts, [p.clone() for p in ps], 5, lr=lr, persistent=True).run(5)
+    np.testing.assert_allclose(a.losses(), b.losses(), rtol=1e-5)
+    for i in range(3):
+        for x, y in zip(a.params_of(i).tensors(), b.params_of(i).tensors()):
+            assert torch.allclose(x, y, rtol=1e-5, atol=1e-6)
