@@ -180,6 +180,127 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_batched(args):
+    """64 RGB images with ragged sizes (128x96 .. 1920x1080), K = pixels/16,
+    one batched fit (autotuned tile side / persistent launch) against the
+    same fits run one image per launch; equal iterations, so equal PSNR up to
+    FP32 summation order."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import api, autotune, build, synth
+    from paper_2510_05814_gb300.fit import FitBatch
+    build.build()
+    sizes = synth.ragged_sizes(args.images, 4)
+    targets, params = [], []
+    for i, (W, H) in enumerate(sizes):
+        t = synth.polygon_image(W, H, 3, 40, 400 + i, texture_amp=0.1)
+        targets.append(torch.tensor(t, device="cuda"))
+        params.append(api.SMoEParams.from_numpy(synth.init_params(t, (W * H) // 16, 5.0, True, 400 + i)))
+    lr = synth.PAPER_LR
+    tr = autotune.tune(targets, params, lr, tiles=(8, 16, 32), persistent=(False, True))
+    n = args.iters
+    # batched: graph of `chunk` iterations replayed
+    fb = FitBatch(targets, [p.clone() for p in params], n, lr=lr, tile=tr.tile,
+                  persistent=tr.persistent, deterministic=True)
+    chunk = 25
+    fb.capture(chunk)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n // chunk):
+        fb.graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    assert fb.status_code() == 0
+    t_batched = e0.elapsed_time(e1) / 1e3
+    # plain: each image alone, one image per launch, same iterations
+    t_plain = 0.0
+    psnr_b, psnr_p, lat_plain = [], [], []
+    for b in range(len(targets)):
+        one = FitBatch([targets[b]], [params[b].clone()], n, lr=lr, tile=tr.tile,
+                       deterministic=True)
+        one.capture(chunk)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(n // chunk):
+            one.graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t_plain += e0.elapsed_time(e1) / 1e3
+        lat_plain.append(t_plain)
+        assert one.status_code() == 0
+        C, H, W = targets[b].shape
+        yb, _, _ = api.render(fb.params_of(b), W, H, tile=tr.tile)
+        yp, _, _ = api.render(one.params_of(0), W, H, tile=tr.tile)
+        from paper_2510_05814_gb300.serve import synth_psnr
+        tb = targets[b].cpu().numpy()
+        psnr_b.append(synth_psnr(yb.cpu().numpy(), tb))
+        psnr_p.append(synth_psnr(yp.cpu().numpy(), tb))
+        del one
+    # pairs per iteration of the batch (lists of the final parameters)
+    pairs = 0
+    for b in range(len(targets)):
+        C, H, W = targets[b].shape
+        r = api.Rasterizer(api.RasterDesc(W, H, C, tr.tile, True), params[b].K).bin(fb.params_of(b))
+        pairs += evaluated_pairs(r.tile_off.cpu().numpy(), W, H, tr.tile)
+    dpsnr = float(np.max(np.abs(np.array(psnr_b) - np.array(psnr_p))))
+    print(json.dumps({
+        "metric": "batched fit: fwd+bwd Gpix·kernel evals/s and fit latency vs one image per launch",
+        "mode": "batched", "images": len(targets), "iters": n,
+        "pixels": int(sum(t.shape[1] * t.shape[2] for t in targets)),
+        "kernels": int(sum(p.K for p in params)), "pairs_per_iter": int(pairs),
+        "autotune": {"tile": tr.tile, "persistent": tr.persistent,
+                     "table_ms_per_iter": [[a, bool(b_), c] for a, b_, _, c in tr.table]},
+        "batched": {"s": t_batched, "ms_per_iter": 1e3 * t_batched / n,
+                    "value": pairs * n / t_batched / 1e9, "latency_all_s": t_batched},
+        "plain": {"s": t_plain, "ms_per_iter": 1e3 * t_plain / n,
+                  "value": pairs * n / t_plain / 1e9,
+                  "latency_p50_s": float(np.percentile(lat_plain, 50)),
+                  "latency_p99_s": float(np.percentile(lat_plain, 99))},
+        "speedup": t_plain / t_batched,
+        "psnr_mean_db": float(np.mean(psnr_b)), "max_abs_psnr_diff_db": dpsnr,
+        "unit": UNIT, "data": "synthetic", "dtype": "f32",
+    }), flush=True)
+
+
+def run_serve(args):
+    """Poisson arrivals (50 req/s): fit requests (ragged sizes, half of them
+    denoising with N(0, 0.05) noise, `iters` Adam steps) and render requests
+    (a fitted model at 1-4x); continuous batching vs one request at a time."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import build, serve
+    build.build()
+    reqs = serve.poisson_workload(args.fits, args.renders, args.rate, iters=args.iters,
+                                  sizes=None)
+    srv = serve.Server(args.budget_gb * (1 << 30), chunk=25)
+    t0 = time.perf_counter()
+    res_b = srv.run(reqs, realtime=True)
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_p = serve.serve_plain(reqs, realtime=True)
+    t_p = time.perf_counter() - t0
+    byid = lambda rs: {r.rid: r for r in rs}
+    rb, rp = byid(res_b), byid(res_p)
+    fits = [r.rid for r in reqs if isinstance(r, serve.FitRequest)]
+    dpsnr = max(abs(rb[i].psnr - rp[i].psnr) for i in fits)
+    split = lambda rs, k: [r for r in rs if r.kind == k]
+    print(json.dumps({
+        "metric": "serving: fit/render request latency p50/p99 and throughput, continuous "
+                  "batching vs one request at a time", "mode": "serve",
+        "requests": len(reqs), "fits": len(fits), "rate_per_s": args.rate, "iters": args.iters,
+        "batched": {"wall_s": t_b, "req_per_s": len(reqs) / t_b,
+                    "all": serve.latency_stats(res_b), "fit": serve.latency_stats(split(res_b, "fit")),
+                    "render": serve.latency_stats(split(res_b, "render"))},
+        "plain": {"wall_s": t_p, "req_per_s": len(reqs) / t_p,
+                  "all": serve.latency_stats(res_p), "fit": serve.latency_stats(split(res_p, "fit")),
+                  "render": serve.latency_stats(split(res_p, "render"))},
+        "max_abs_psnr_diff_db": float(dpsnr),
+        "psnr_mean_db": float(np.mean([rb[i].psnr for i in fits])),
+        "data": "synthetic", "dtype": "f32",
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,10 +310,25 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--mode", default="fit", choices=["fit", "batched", "serve"],
+                    help="fit: the 2048^2 fit step (default); batched: 64 ragged images; "
+                         "serve: Poisson request stream")
+    ap.add_argument("--images", type=int, default=64)
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--fits", type=int, default=40)
+    ap.add_argument("--renders", type=int, default=40)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batched":
+        args.iters = args.iters or 200
+        return run_batched(args)
+    if args.mode == "serve":
+        args.iters = args.iters or 500
+        return run_serve(args)
 
     import numpy as np
     import torch

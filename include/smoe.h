@@ -182,6 +182,11 @@ typedef struct {
     int32_t hist;           /* columns of `loss` */
     int32_t persistent;     /* 1: the fused tile kernel runs as one persistent grid that
                                takes tiles from a work queue; 0: one CTA per tile */
+    int32_t deterministic;  /* 1: every (tile, kernel) pair writes its partial gradient
+                               sums to its own slot and the Adam step adds them in a fixed
+                               tile order, so a fit is bit-reproducible and independent of
+                               the other images in the batch (costs 64 B per pair of
+                               workspace); 0: float atomics (faster, order-dependent) */
 } smoe_fit_batch;
 
 /* Workspace bytes for a fit of this batch with pair_cap pairs in total. */

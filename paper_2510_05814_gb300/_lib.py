@@ -47,7 +47,7 @@ class FitBatch(ctypes.Structure):
                 ("expert", ctypes.c_int32), ("qmax", ctypes.c_float), ("b1", ctypes.c_double),
                 ("b2", ctypes.c_double), ("eps", ctypes.c_double), ("step", ctypes.c_void_p),
                 ("loss", ctypes.c_void_p), ("hist", ctypes.c_int32),
-                ("persistent", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
 
 
 _lib = None

@@ -101,7 +101,9 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
             float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
                               0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float *acc = w.acc + k * g.GS;
-            const float *s = rc.x <= rc.z ? acc : zero;
+            float gat[16];
+            if (w.part && rc.x <= rc.z) gather_sums(g, w, im, k, rc, gat);
+            const float *s = rc.x > rc.z ? zero : (w.part ? gat : acc);
             const float *r = w.rec + k * g.S;
             const int C = g.C, E = g.linear ? 3 : 1;
             const float *cf = coef + 8 * b;
@@ -141,7 +143,8 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
                 adam1(pv, -s[d], mv, vv, kch);
                 chol[3 * kl + d] = pv; m_chol[3 * kl + d] = mv; v_chol[3 * kl + d] = vv;
             }
-            for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
+            if (!w.part)
+                for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
         }
     }
     // Step counters advance once every CTA has read them.

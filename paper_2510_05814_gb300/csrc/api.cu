@@ -24,11 +24,12 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 // Workspace regions, in order; `fit` adds the batch table and the lists.
 struct Layout {
     size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
-    size_t table, tile_off, pair_k, n_pairs, done, work, coef;
+    size_t table, tile_off, pair_k, n_pairs, done, work, coef, part;
     size_t total;
 };
 
-Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, bool fit) {
+Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, bool fit,
+              bool det = false) {
     Layout L{};
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
@@ -49,6 +50,7 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
         L.done = take(sizeof(uint32_t));
         L.work = take(sizeof(uint32_t));
         L.coef = take(sizeof(float) * 8 * (size_t)B);
+        L.part = det ? take(sizeof(float) * (size_t)GS * (size_t)pair_cap) : 0;
     }
     L.total = o;
     return L;
@@ -281,7 +283,8 @@ smoe_status smoe_fit_workspace_size(const smoe_fit_batch *batch, const smoe_fit_
     std::vector<ImgDev> tab;
     if (!fit_geo(batch, imgs, &g, &tab) || pair_cap < 0 || pair_cap > 0x7fffffffLL || !bytes)
         return SMOE_ERR_ARG;
-    *bytes = layout(g.K_total, g.tiles_total, pair_cap, g.S, g.GS, g.B, true).total;
+    *bytes = layout(g.K_total, g.tiles_total, pair_cap, g.S, g.GS, g.B, true,
+                    batch->deterministic != 0).total;
     return SMOE_OK;
 }
 
@@ -290,7 +293,8 @@ static smoe_status fit_bufs(const smoe_fit_batch *batch, const smoe_fit_image *i
                             Geo *g, Bufs *w, Layout *L, std::vector<ImgDev> *tab) {
     if (!fit_geo(batch, imgs, g, tab) || pair_cap < 0 || pair_cap > 0x7fffffffLL || !status)
         return SMOE_ERR_ARG;
-    *L = layout(g->K_total, g->tiles_total, pair_cap, g->S, g->GS, g->B, true);
+    *L = layout(g->K_total, g->tiles_total, pair_cap, g->S, g->GS, g->B, true,
+                batch->deterministic != 0);
     if (!ws_ok(ws, ws_bytes, L->total)) return SMOE_ERR_WORKSPACE;
     char *b = static_cast<char *>(ws);
     if (g->B > 1) g->table = reinterpret_cast<const ImgDev *>(b + L->table);
@@ -299,6 +303,7 @@ static smoe_status fit_bufs(const smoe_fit_batch *batch, const smoe_fit_image *i
     w->pair_k = reinterpret_cast<int32_t *>(b + L->pair_k);
     w->n_pairs = reinterpret_cast<int64_t *>(b + L->n_pairs);
     w->work = reinterpret_cast<uint32_t *>(b + L->work);
+    w->part = batch->deterministic ? reinterpret_cast<float *>(b + L->part) : nullptr;
     w->pair_cap = pair_cap;
     w->status = status;
     return SMOE_OK;

@@ -519,11 +519,27 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                 }
             }
             if (m) {
-                float4 *dst = reinterpret_cast<float4 *>(w.acc + (int64_t)sm.kid[j] * R::GS);
+                if (w.part) {        // deterministic: this pair's own slot
+                    float4 *dst = reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS);
 #pragma unroll
-                for (int q = 0; q < R::GS / 4; ++q)
-                    atomicAdd(dst + q, make_float4(acc.v[4 * q], acc.v[4 * q + 1], acc.v[4 * q + 2],
-                                                   acc.v[4 * q + 3]));
+                    for (int q = 0; q < R::GS / 4; ++q)
+                        dst[q] = make_float4(acc.v[4 * q], acc.v[4 * q + 1], acc.v[4 * q + 2],
+                                             acc.v[4 * q + 3]);
+                } else {
+                    float4 *dst = reinterpret_cast<float4 *>(w.acc + (int64_t)sm.kid[j] * R::GS);
+#pragma unroll
+                    for (int q = 0; q < R::GS / 4; ++q)
+                        atomicAdd(dst + q, make_float4(acc.v[4 * q], acc.v[4 * q + 1],
+                                                       acc.v[4 * q + 2], acc.v[4 * q + 3]));
+                }
+            }
+        }
+        if (w.part) {                // pairs whose kernel misses every row add zero
+            for (int i = threadIdx.x; i < nc * (R::GS / 4); i += kThreads) {
+                const int j = i / (R::GS / 4), q = i - j * (R::GS / 4);
+                if (!sm.mask[j])
+                    reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS)[q] =
+                        make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
     }

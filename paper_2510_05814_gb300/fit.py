@@ -21,11 +21,17 @@ class FitBatch:
     targets: list of (C,H,W) float32 CUDA tensors; params: list of SMoEParams
     (each image's own tensors, updated in place); iters: per-image run length
     (int or list); lr = (mu0, mu1, chol, ea, eW) or one tuple per image;
-    persistent: run the fused tile kernel as one persistent grid."""
+    persistent: run the fused tile kernel as one persistent grid;
+    deterministic: per-pair gradient partials added in a fixed order (a fit
+    is then bit-reproducible and independent of the rest of the batch)."""
 
     def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
                  qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
-                 persistent=False, pair_cap=None, device="cuda"):
+                 persistent=False, pair_cap=None, moments=None, steps=None,
+                 deterministic=False, device="cuda"):
+        """moments: optional list of (m, v) SMoEParams per image and steps an
+        optional list of iterations already done: a run that continues in a
+        re-formed batch keeps its Adam state and schedule position."""
         assert len(targets) == len(params) and len(targets) > 0
         self.B = len(targets)
         self.device = device
@@ -34,14 +40,21 @@ class FitBatch:
         self.tile, self.qmax = tile, qmax
         self.b1, self.b2, self.eps = b1, b2, eps
         self.persistent = bool(persistent)
+        self.deterministic = bool(deterministic)
         self.targets = [t.contiguous() for t in targets]
         self.iters = [iters] * self.B if np.isscalar(iters) else list(iters)
         self.lr = [lr] * self.B if np.isscalar(lr[0]) else list(lr)
         self.params = list(params)
         self.Ks = [p.K for p in params]
-        self.m = [p.zeros_like() for p in params]
-        self.v = [p.zeros_like() for p in params]
-        self.step = torch.zeros(self.B, dtype=torch.int32, device=device)
+        if moments is None:
+            self.m = [p.zeros_like() for p in params]
+            self.v = [p.zeros_like() for p in params]
+        else:
+            self.m = [mv[0] for mv in moments]
+            self.v = [mv[1] for mv in moments]
+        self.step = torch.tensor(list(steps) if steps is not None else [0] * self.B,
+                                 dtype=torch.int32, device=device)
+        self._continue = moments is not None
         self.hist = int(hist if hist is not None else max(self.iters))
         self.loss = torch.zeros(self.B, max(self.hist, 1), dtype=torch.float64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
@@ -56,7 +69,7 @@ class FitBatch:
                 total += int(r.n_pairs.item())
             pair_cap = int(total * pair_slack) + 4096
         self.pair_cap = int(pair_cap)
-        self._setup(reset=True)
+        self._setup(reset=not self._continue)
 
     # -- C structs
     def _structs(self):
@@ -69,7 +82,7 @@ class FitBatch:
                                     lr[1], lr[2], lr[3], lr[4])
         batch = _lib.FitBatch(self.B, self.C, self.tile, int(self.linear), self.qmax, self.b1,
                               self.b2, self.eps, _ptr(self.step), _ptr(self.loss), self.hist,
-                              int(self.persistent))
+                              int(self.persistent), int(self.deterministic))
         return batch, imgs
 
     def _setup(self, reset):
@@ -83,6 +96,7 @@ class FitBatch:
         self.ws = raw[off:off + n.value]
         if not reset:
             self.status.zero_()
+            self.loss.zero_()
         check(lib.smoe_fit_init(ctypes.byref(self._batch), self._imgs, self.pair_cap,
                                 _ptr(self.ws), self.ws.numel(), int(reset), _ptr(self.status),
                                 _stream(None)), "smoe_fit_init")

@@ -321,3 +321,29 @@ def test_persistent_launch_equals_grid_launch():
     for i in range(3):
         for x, y in zip(a.params_of(i).tensors(), b.params_of(i).tensors()):
             assert torch.allclose(x, y, rtol=1e-5, atol=1e-6)
+
+
+def test_deterministic_fit_is_bit_reproducible_and_batch_independent():
+    """Deterministic accumulation: two runs agree bit for bit, and an image
+    fitted in a ragged batch equals the same image fitted alone."""
+    sizes = [(80, 60), (50, 70), (120, 40)]
+    ts, ps = [], []
+    for i, (W, H) in enumerate(sizes):
+        t = synth.polygon_image(W, H, 3, 5, 500 + i, texture_amp=0.1)
+        ts.append(torch.tensor(t, device="cuda"))
+        ps.append(api.SMoEParams.from_numpy(synth.init_params(t, (W * H) // 16, 3.0, True, 500 + i)))
+    lr = (1e-2, 1e-3, 1e-2, 1e-2, 1e-2)
+    a = FitBatch(ts, [p.clone() for p in ps], 12, lr=lr, deterministic=True).run(12)
+    b = FitBatch(ts, [p.clone() for p in ps], 12, lr=lr, deterministic=True,
+                 persistent=True).run(12, graph_iters=4)
+    for i in range(3):
+        for x, y in zip(a.params_of(i).tensors(), b.params_of(i).tensors()):
+            assert torch.equal(x, y)
+    one = FitBatch([ts[1]], [ps[1].clone()], 12, lr=lr, deterministic=True).run(12)
+    for x, y in zip(a.params_of(1).tensors(), one.params_of(0).tensors()):
+        assert torch.equal(x, y)
+    # the reported MSE adds per-tile FP64 partial sums in completion order
+    np.testing.assert_allclose(a.losses()[1], one.losses()[0], rtol=1e-12)
+    # and the deterministic sums agree with the atomic ones to FP32 rounding
+    c = FitBatch(ts, [p.clone() for p in ps], 12, lr=lr, deterministic=False).run(12)
+    np.testing.assert_allclose(c.losses(), a.losses(), rtol=1e-5)

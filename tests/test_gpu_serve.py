@@ -1,0 +1,76 @@
+"""Serving with continuous batching: every result is the same served in the
+mix as run alone (one request at a time, one image per launch)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2510_05814_gb300 import serve, synth  # noqa: E402
+from paper_2510_05814_gb300.serve import FitRequest, RenderRequest  # noqa: E402
+
+# The server fits in the deterministic accumulation mode (per-pair partial
+# sums added in a fixed tile order), so an image's fit does not depend on
+# the other images of its batch: fitted and rendered images must be
+# bit-identical.  The reported per-iteration MSE adds per-tile FP64 partial
+# sums in completion order, so it is held to FP64 rounding.
+TOL_Y = 0.0
+TOL_LOSS = 1e-12
+
+
+def requests():
+    rng = np.random.default_rng(7)
+    sizes = [(96, 64), (160, 120), (64, 80)]
+    iters = [10, 30, 30]
+    reqs = []
+    for i, ((W, H), n) in enumerate(zip(sizes, iters)):
+        img = synth.polygon_image(W, H, 3, 6, 300 + i, texture_amp=0.1)
+        den = i == 1
+        if den:
+            img = (img + rng.normal(0, np.sqrt(0.05), img.shape)).astype(np.float32)
+        reqs.append(FitRequest(i, img, iters=n, sigma=3.0, denoise=den, arrival=0.0, seed=i))
+    reqs.append(RenderRequest(3, model=0, scale=2.0, arrival=0.0))
+    reqs.append(RenderRequest(4, model=1, scale=1.5, arrival=0.0))
+    reqs.append(RenderRequest(5, model=2, scale=3.25, arrival=0.0))
+    return reqs
+
+
+def test_served_results_equal_alone():
+    reqs = requests()
+    # room for the first two fits only: the third joins when the first leaves,
+    # while the second continues in the re-formed batch
+    b = [serve.fit_bytes(3, r.image.shape[1], r.image.shape[2],
+                         r.image.shape[1] * r.image.shape[2] // 16) for r in reqs[:3]]
+    srv = serve.Server(b[0] + b[1] + 1, chunk=10, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))
+    mixed = {r.rid: r for r in srv.run(reqs, realtime=False)}
+    alone = {r.rid: r for r in serve.serve_plain(reqs, realtime=False,
+                                                 lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))}
+    assert sorted(mixed) == sorted(alone) == list(range(6))
+    ev = [e for _, e in srv.events]
+    assert ev.index("admit fit 2") > ev.index("finish fit 0")
+    assert ev.index("admit fit 2") < ev.index("finish fit 1")
+    for rid in range(6):
+        a, m = alone[rid], mixed[rid]
+        assert a.output.shape == m.output.shape
+        assert np.max(np.abs(a.output - m.output)) <= TOL_Y, rid
+        if a.kind == "fit":
+            np.testing.assert_allclose(m.losses, a.losses, rtol=TOL_LOSS)
+            assert a.psnr == m.psnr        # computed on the host from equal images
+    assert mixed[3].output.shape == (3, 128, 192)      # 2x super-resolution of 96x64
+
+
+def test_budget_limits_concurrent_fits():
+    reqs = [r for r in requests() if isinstance(r, FitRequest)]
+    b = serve.fit_bytes(3, 120, 160, 120 * 160 // 16)
+    srv = serve.Server(b + 1, chunk=10, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))
+    srv.run(reqs, realtime=False)
+    live, peak = 0, 0
+    for _, e in srv.events:
+        if e.startswith("admit fit"):
+            live += 1
+        elif e.startswith("finish fit"):
+            live -= 1
+        peak = max(peak, live)
+    assert peak == 1
