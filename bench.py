@@ -39,10 +39,32 @@ UNIT = "Gpix·kernel evals/s"
 WORKLOAD = ("rgb2048_K262144_linear_aniso: 2048x2048 RGB fp32, 40 ramp polygons + Perlin "
             "texture 0.1, K=262144 anisotropic kernels (area sigma 5 px, aspect 1-3), linear "
             "experts, 16x16 tiles, q_max 9, Adam at the paper's rates")
-MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM, measured on GB300 (sm_103)
-# DRAM bytes per launch of the fused tile kernel from one ncu capture (see
-# profiles/); valid only while render.cu is the file that was profiled.
-TRAFFIC = {"render_cu_sha256": None, "bytes_per_launch": None}
+MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measurement fails
+# Kernels launched by one fit step: binning (bbox, scan reduce/top/down,
+# scatter, warp sort, long-list sort), the fused tile kernel, fused Adam.
+KERNELS_PER_STEP = 9
+# From one ncu capture of the fused tile kernel on this workload (profiles/):
+# DRAM bytes per launch and pipe utilisation; valid only while render.cu is
+# the file that was profiled.
+NCU = {"render_cu_sha256": None, "bytes_per_launch": None, "fma_pipe_active": None,
+       "issue_active": None, "xu_active": None}
+
+
+def issue_rates():
+    """Measured lane operations per clock per SM of ex2 / FFMA / packed
+    f32x2 FMA (libsmoe_rates.so), or None."""
+    import ctypes
+    from paper_2510_05814_gb300 import build
+    try:
+        lib = ctypes.CDLL(build.RATES_LIB)
+    except OSError:
+        return None
+    out = (ctypes.c_double * 3)()
+    clk = ctypes.c_double(0.0)
+    lib.smoe_issue_rates.restype = ctypes.c_int
+    if lib.smoe_issue_rates(out, ctypes.byref(clk)) != 0:
+        return None
+    return {"ex2": out[0], "ffma": out[1], "ffma2": out[2], "clock_mhz": clk.value}
 
 
 def sha256(path):
@@ -263,6 +285,60 @@ def run_batched(args):
     }), flush=True)
 
 
+def run_denoise(args):
+    """MM-RSMoE denoising (Sec. V-C) on the synthetic 768x512 RGB stand-in
+    for the paper's test images: for each noise variance of Table III and
+    each model count H, the H fits of the noisy image run as one batch
+    (CUDA-graph replays of 25 iterations) and the fused render follows;
+    reports PSNR of the noisy and the fused image against the clean one and
+    the GPU time of fit + fusion."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import build, denoise, synth
+    from paper_2510_05814_gb300.fit import FitBatch
+    build.build()
+    W, H = 768, 512
+    K = W * H // 64
+    n = args.iters
+    chunk = 25
+
+    def psnr(y, c):
+        mse = float(((y.clamp(0.0, 1.0) - c) ** 2).mean())
+        return 10.0 * np.log10(1.0 / mse)
+
+    rows = []
+    for var in (0.0037, 0.005, 0.01, 0.05):
+        clean, noisy = synth.denoise_case(W, H, var, seed=5)
+        c = torch.tensor(clean, device="cuda")
+        tn = torch.tensor(noisy, device="cuda")
+        for nm in args.models:
+            models = denoise.init_models(noisy, nm, K, 5.0, True, seed=500)
+            fb = FitBatch([tn] * nm, models, n, lr=synth.PAPER_LR, tile=16)
+            fb.capture(chunk)
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            for _ in range(n // chunk):
+                fb.graph.replay()
+            e[1].record()
+            y = fb.render_mean()
+            e[2].record()
+            torch.cuda.synchronize()
+            assert fb.status_code() == 0
+            rows.append({"noise_var": var, "models": nm, "psnr_noisy_db": psnr(tn, c),
+                         "psnr_db": psnr(y, c), "fit_s": e[0].elapsed_time(e[1]) / 1e3,
+                         "fuse_ms": e[1].elapsed_time(e[2]),
+                         "ms_per_iter": e[0].elapsed_time(e[1]) / n})
+            del fb, models, y
+    print(json.dumps({
+        "metric": "MM-RSMoE denoising: PSNR of the fused image and GPU time of H fits + fusion",
+        "mode": "denoise", "image": f"{W}x{H}x3 synthetic (30 ramp polygons + Perlin 0.1, "
+                                    f"clipped to [0,1]) + N(0, var) noise",
+        "kernels_per_model": K, "iters": n, "lr": list(synth.PAPER_LR), "tile": 16,
+        "rows": rows, "data": "synthetic", "dtype": "f32",
+    }), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals (50 req/s): fit requests (ragged sizes, half of them
     denoising with N(0, 0.05) noise, `iters` Adam steps) and render requests
@@ -310,9 +386,11 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--mode", default="fit", choices=["fit", "batched", "serve"],
+    ap.add_argument("--mode", default="fit", choices=["fit", "batched", "serve", "denoise"],
                     help="fit: the 2048^2 fit step (default); batched: 64 ragged images; "
-                         "serve: Poisson request stream")
+                         "serve: Poisson request stream; denoise: MM-RSMoE")
+    ap.add_argument("--models", type=int, nargs="+", default=[1, 8, 16, 64],
+                    help="denoise: model counts H")
     ap.add_argument("--images", type=int, default=64)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--fits", type=int, default=40)
@@ -329,6 +407,9 @@ def main():
     if args.mode == "serve":
         args.iters = args.iters or 500
         return run_serve(args)
+    if args.mode == "denoise":
+        args.iters = args.iters or 2000
+        return run_denoise(args)
 
     import numpy as np
     import torch
@@ -361,6 +442,7 @@ def main():
     torch.cuda.synchronize()
     assert fb.status_code() == 0
     pairs0, lists0 = pairs_now()
+    rates = issue_rates()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -446,13 +528,16 @@ def main():
     if not sm_max and os.path.exists(peaks_path):
         sm_max = json.load(open(peaks_path)).get("sm_max_mhz")
     sm_max = sm_max or 2070.0
-    ex2_peak = MUFU_PER_CLK_PER_SM * sms * sm_max * 1e6            # ex2 / s
+    sm_load = clocks.get("sm_mhz") or sm_max                      # median SM clock under load
+    mufu = rates["ex2"] if rates else MUFU_PER_CLK_PER_SM
+    ex2_peak = mufu * sms * sm_load * 1e6                          # ex2 / s
     tile_s = statistics.mean(tile_ms) / 1e3
     ex2_achieved = 2.0 * pairs_step / tile_s                       # fwd + bwd: 2 ex2 / pair
-    traffic = None
-    if TRAFFIC["render_cu_sha256"] and TRAFFIC["render_cu_sha256"] == sha256(
+    ncu = None
+    if NCU["render_cu_sha256"] and NCU["render_cu_sha256"] == sha256(
             os.path.join(ROOT, "paper_2510_05814_gb300", "csrc", "render.cu")):
-        traffic = TRAFFIC["bytes_per_launch"]
+        ncu = NCU
+    traffic = ncu["bytes_per_launch"] if ncu else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -475,8 +560,16 @@ def main():
                          "achieved": ex2_achieved / 1e9, "peak": ex2_peak / 1e9,
                          "unit": "Gex2/s", "frac": ex2_achieved / ex2_peak,
                          "traffic": traffic,
-                         "peak_basis": f"{MUFU_PER_CLK_PER_SM} ex2/clk/SM x {sms} SMs x "
-                                       f"{sm_max:.0f} MHz; 2 ex2 per fwd+bwd pair"},
+                         "peak_basis": (f"{mufu:.1f} ex2 lanes/clk/SM "
+                                        f"({'measured live, libsmoe_rates' if rates else 'fallback'})"
+                                        f" x {sms} SMs x {sm_load:.0f} MHz (median under load); "
+                                        "2 ex2 per listed fwd+bwd pair"),
+                         "issue_rates_per_clk_per_sm": rates,
+                         "ncu_pipes": None if ncu is None else {
+                             "fma_pipe_active": ncu["fma_pipe_active"],
+                             "issue_active": ncu["issue_active"],
+                             "xu_active": ncu["xu_active"]}},
+            "value_fwd_bwd_only": pairs_step / tile_s / 1e9,
             "phases_ms": {"bin": statistics.mean(bin_ms), "fused_tiles": statistics.mean(tile_ms),
                           "adam": statistics.mean(adam_ms)},
             "fit_iters_per_s": args.steps / tot_s,
@@ -485,7 +578,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 8},
-            "gpu_launches": 8 * args.steps,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(out), flush=True)

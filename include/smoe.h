@@ -229,6 +229,25 @@ SMOE_API smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_
                                     int64_t pair_cap, void *ws, size_t ws_bytes, int32_t phase,
                                     int32_t *status, void *stream);
 
+/* Multi-model fusion for denoising (Sec. V-C, Eq. 11): y_m = (1/H) sum_h y_h,
+ * the per-pixel mean of the renders of the H = batch->B models of a fit
+ * batch whose images all have one size W x H (the H models of MM-RSMoE are
+ * fits of one noisy image from differently shifted initial kernel lattices).
+ * The call bins the models' current parameters (as phase 0 does, into the
+ * batch's lists) and renders the mean in one launch, one CTA per output tile
+ * visiting the H models in index order: y_h is exactly what smoe_render
+ * gives for model h (0 where no kernel of model h is included), and H = 1
+ * returns that render bit for bit.
+ *   batch, imgs, pair_cap, ws, ws_bytes: as smoe_fit_phase, after
+ *                smoe_fit_init on this workspace
+ *   y            out: C x H x W FP32 (device)
+ *   status       device status word: a pair count above pair_cap sets
+ *                SMOE_ERR_CAPACITY and y is then not written
+ * Returns SMOE_ERR_ARG if the images differ in size. */
+SMOE_API smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                          int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
+                                          int32_t *status, void *stream);
+
 /* Bin and render one model without allocating anything: for callers that
  * cannot call cudaMalloc (a plugin inside an application that owns every
  * device allocation, code that must not touch the allocator).  The paper has

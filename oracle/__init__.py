@@ -179,6 +179,27 @@ def render(m: Model, pixels=None, with_scale=False):
     return (y, invd, absm) if with_scale else (y, invd)
 
 
+def render_mean(models, pixels=None, with_scale=False):
+    """Multi-model fusion (Sec. V-C, Eq. 11) in FP64: y_m = (1/H) sum_h y_h
+    over the H models, each y_h exactly as `render` gives it (0 at a pixel
+    where model h includes no kernel).  Layout as `render`'s y; with_scale
+    also returns the mean over the models of `render`'s term-magnitude sum."""
+    outs = [render(m, pixels, with_scale=True) for m in models]
+    y = np.sum([o[0] for o in outs], axis=0) / len(models)
+    if not with_scale:
+        return y
+    return y, np.sum([np.maximum(np.abs(o[0]), o[2]) for o in outs], axis=0) / len(models)
+
+
+def mm_denoise(models, noisy, n_it, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3)):
+    """MM-RSMoE denoising (Sec. V-C): each of the H models (the same kernel
+    count, initial lattices shifted against each other) is fitted to the one
+    noisy image by `fit`, then the H renders are fused by Eq. 11.  Updates
+    the models in place; returns (y_m, per-model loss histories)."""
+    losses = [fit(m, noisy, n_it, lr=lr) for m in models]
+    return render_mean(models), losses
+
+
 def backward(m: Model, gy=None, target=None, kernels=None, with_scale=False):
     """FP64 gradient of the loss w.r.t. (mu, chol, ea, eW) in API units.
 

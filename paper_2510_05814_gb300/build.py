@@ -19,6 +19,9 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsmoe.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["bin.cu", "render.cu", "adam.cu", "api.cu", "static_render.cu"]
+# Issue-rate micro-benchmark (the ALU roofline's per-clock peaks), its own library.
+RATES_SRC = "issue_rates.cu"
+RATES_LIB = os.path.join(HERE, "libsmoe_rates.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE]
@@ -38,9 +41,9 @@ def _deps():
 
 
 def needs_build() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(RATES_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(RATES_LIB))
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
@@ -60,8 +63,19 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    def rates_lib():
+        tmp = RATES_LIB + ".tmp%d" % os.getpid()
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-shared", os.path.join(CSRC, RATES_SRC), "-o", tmp,
+               "-cudart", "static"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {RATES_SRC}:\n{r.stderr}")
+        os.replace(tmp, RATES_LIB)
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        rates = ex.submit(rates_lib)
         objs = list(ex.map(compile_one, SOURCES))
+        rates.result()
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)

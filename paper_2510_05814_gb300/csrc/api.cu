@@ -399,6 +399,24 @@ smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_image *im
         fit_phase(batch, g, w, done, coef, phase, static_cast<cudaStream_t>(stream)));
 }
 
+smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                 int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
+                                 int32_t *status, void *stream) {
+    Geo g;
+    Bufs w;
+    Layout L;
+    std::vector<ImgDev> tab;
+    if (!y) return SMOE_ERR_ARG;
+    smoe_status s = fit_bufs(batch, imgs, pair_cap, ws, ws_bytes, status, &g, &w, &L, &tab);
+    if (s != SMOE_OK) return s;
+    for (int b = 1; b < batch->B; ++b)
+        if (imgs[b].W != imgs[0].W || imgs[b].H != imgs[0].H) return SMOE_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_bin(g, w, st);
+    if (e == cudaSuccess) e = launch_render_mean(g, w, y, st);
+    return cuda_status(e);
+}
+
 smoe_status smoe_get_status(const int32_t *status, void *stream) {
     if (!status) return SMOE_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -340,6 +340,62 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(const __grid_co
     }
 }
 
+// Multi-model fusion (Sec. V-C, Eq. 11): the B models of a batch whose
+// images share one size are rendered tile by tile and averaged per pixel,
+// y = (sum_h y_h) / B, with y_h = N_h / D_h (0 where D_h = 0) exactly as
+// k_render computes it.  The models are visited in index order, so the sum
+// is deterministic, and B = 1 gives k_render's output bit for bit.  The grid
+// covers the tiles of one image; image b's tiles follow image b-1's.
+template <int C, bool LIN, int T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_mean(const __grid_constant__ Geo g, Bufs w,
+                                                             float *__restrict__ y) {
+    using G = Geom<C, T>;
+    if (status_bad(w.status)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
+    const int64_t tiles_img = g.tiles_total / g.B;
+    float2 Sv[G::BPW][C];
+#pragma unroll
+    for (int bi = 0; bi < G::BPW; ++bi)
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) Sv[bi][ch] = f2(0.0f);
+    TileInfo ti{};
+    for (int b = 0; b < g.B; ++b) {
+        if (b > 0) __syncthreads();               // the previous model's chunk is consumed
+        ti = tile_info(g, w, (int64_t)b * tiles_img + blockIdx.x);
+        float2 Dv[G::BPW], Nv[G::BPW][C];
+        fwd_tile<C, LIN, T>(g, w, ti, sm, Dv, Nv);
+#pragma unroll
+        for (int bi = 0; bi < G::BPW; ++bi) {
+            const float ia = Dv[bi].x > 0.0f ? 1.0f / Dv[bi].x : 0.0f;
+            const float ib = Dv[bi].y > 0.0f ? 1.0f / Dv[bi].y : 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) {
+                Sv[bi][ch].x = __fadd_rn(Sv[bi][ch].x, __fmul_rn(Nv[bi][ch].x, ia));
+                Sv[bi][ch].y = __fadd_rn(Sv[bi][ch].y, __fmul_rn(Nv[bi][ch].y, ib));
+            }
+        }
+    }
+    const float nb = (float)g.B;
+    const int64_t HW = (int64_t)ti.W * ti.H;
+#pragma unroll
+    for (int bi = 0; bi < G::BPW; ++bi) {
+        int row, col;
+        if (!lane_pixels<C, T>(bi, row, col)) continue;
+        const int yi = ti.y0 + row;
+        if (yi >= ti.H) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xi = ti.x0 + col + h;
+            if (xi >= ti.W) continue;
+            const int64_t o = (int64_t)yi * ti.W + xi;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch)
+                y[ch * HW + o] = __fdiv_rn(h ? Sv[bi][ch].y : Sv[bi][ch].x, nb);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- backward
 
 // Write the state of pixels (row, col), (row, col+1): H_c = G_c / D and
@@ -730,6 +786,10 @@ cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y,
     } else if (which == 2) {
         if ((e = smem_attr(k_fit_tile<C, LIN, T>, smem, a2)) != cudaSuccess) return e;
         k_fit_tile<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, loss, hist, step);
+    } else if (which == 4) {
+        static bool a4 = false;
+        if ((e = smem_attr(k_render_mean<C, LIN, T>, smem, a4)) != cudaSuccess) return e;
+        k_render_mean<C, LIN, T><<<(unsigned)(g.tiles_total / g.B), kThreads, smem, st>>>(g, w, yo);
     } else {
         static bool a3 = false;
         static int resident = 0;
@@ -799,6 +859,10 @@ cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const
     if (g.K_total > 0)
         k_finalize<<<(unsigned)((g.K_total + 255) / 256), 256, 0, st>>>(g, w, grad);
     return cudaGetLastError();
+}
+
+cudaError_t launch_render_mean(const Geo &g, const Bufs &w, float *y, cudaStream_t st) {
+    return dispatch(g, w, 4, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, st);
 }
 
 cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,

@@ -152,6 +152,8 @@ __device__ __forceinline__ bool status_bad(const int32_t *status) {
 cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st);
 cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
                           cudaStream_t st);
+// Mean of the renders of a batch's B models (all images one size), Eq. 11.
+cudaError_t launch_render_mean(const Geo &g, const Bufs &w, float *y, cudaStream_t st);
 cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const float *inv_d,
                               const float *gy, const float *target, const smoe_params &grad,
                               cudaStream_t st);

@@ -95,8 +95,9 @@ class FitBatch:
         off = (-raw.data_ptr()) % 256
         self.ws = raw[off:off + n.value]
         if not reset:
+            # an overflowed iteration stopped at binning: it added no loss and
+            # took no step, so only the status is cleared
             self.status.zero_()
-            self.loss.zero_()
         check(lib.smoe_fit_init(ctypes.byref(self._batch), self._imgs, self.pair_cap,
                                 _ptr(self.ws), self.ws.numel(), int(reset), _ptr(self.status),
                                 _stream(None)), "smoe_fit_init")
@@ -166,6 +167,30 @@ class FitBatch:
                 raise SmoeError(st, "smoe_fit")
             done += chunk
         return self
+
+    def render_mean(self, out=None, stream=None):
+        """Multi-model fusion (Sec. V-C, Eq. 11): the per-pixel mean of the
+        renders of the batch's B models, all images of one size.  Bins the
+        current parameters (growing the pair buffer if they overflow it) and
+        returns a (C, H, W) tensor."""
+        t = self.targets[0]
+        if any(x.shape != t.shape for x in self.targets):
+            raise ValueError("render_mean needs images of one size")
+        out = torch.empty_like(t) if out is None else out
+        assert out.shape == t.shape and out.dtype == torch.float32 and out.is_contiguous()
+        while True:
+            check(_lib.load().smoe_fit_render_mean(ctypes.byref(self._batch), self._imgs,
+                                                   self.pair_cap, _ptr(self.ws), self.ws.numel(),
+                                                   _ptr(out), _ptr(self.status),
+                                                   _stream(stream)), "smoe_fit_render_mean")
+            st = self.status_code()
+            if st == _lib.SMOE_ERR_CAPACITY:
+                self.pair_cap = int(self.pair_cap * 1.5) + 4096
+                self._setup(reset=False)
+                continue
+            if st != _lib.SMOE_OK:
+                raise SmoeError(st, "smoe_fit_render_mean")
+            return out
 
     def losses(self):
         return self.loss.cpu().numpy()

@@ -177,14 +177,19 @@ class Params:
                       None if self.eW is None else self.eW.copy())
 
 
-def init_params(target, K, sigma, linear, seed, aniso=None, slope_std=0.0):
+def init_params(target, K, sigma, linear, seed, aniso=None, slope_std=0.0, offset=(0.0, 0.0)):
     """Initial kernel set for ``target`` (C,H,W): K kernels on a jittered grid,
     round with bandwidth ``sigma`` px (or, with aniso=(lo, hi), random
     orientation and aspect ratio in [lo, hi] at the same area), experts set to
-    the target at the nearest pixel, slopes zero (or N(0, slope_std))."""
+    the target at the nearest pixel, slopes zero (or N(0, slope_std)).
+    ``offset`` = (ox, oy) pixels shifts the whole grid (wrapping around the
+    image), the shifted initial lattice of one model of a multi-model set."""
     C, H, W = target.shape
     gx, gy = grid_shape(K, W, H)
     mu = jittered_grid(gx, gy, seed)
+    if offset[0] or offset[1]:
+        mu = np.mod(mu.astype(np.float64) + np.array([offset[0] / W, offset[1] / H]), 1.0)
+        mu = mu.astype(np.float32)
     rng = np.random.default_rng(seed + 7919)
     if aniso is None:
         chol = np.zeros((K, 3), np.float64)
@@ -246,6 +251,17 @@ def rgb_2048(seed=3, aniso=(1.0, 3.0), slope_std=2e-3):
     t = polygon_image(2048, 2048, 3, 40, seed, texture_amp=0.1)
     p = init_params(t, 262144, 5.0, True, seed, aniso=aniso, slope_std=slope_std)
     return Workload("rgb2048_K262144_linear_aniso", t, p, 16, 9.0, 1, PAPER_LR)
+
+
+def denoise_case(W=768, H=512, noise_var=0.01, seed=5):
+    """Denoising input at the size of the paper's 768x512 RGB test images:
+    a clean synthetic image (30 ramp polygons + Perlin texture 0.1, values
+    clipped to [0, 1]) and the same image plus N(0, noise_var) noise (not
+    clipped).  Returns (clean, noisy), each (3, H, W) float32."""
+    clean = np.clip(polygon_image(W, H, 3, 30, seed, texture_amp=0.1), 0.0, 1.0)
+    rng = np.random.default_rng(seed + 104729)
+    noisy = clean + rng.normal(0.0, math.sqrt(noise_var), clean.shape)
+    return clean.astype(np.float32), noisy.astype(np.float32)
 
 
 def ragged_sizes(n=64, seed=4):

@@ -539,3 +539,63 @@ def test_flop_convention_from_tables():
     assert len(rows) >= 7
     for avg, flops in rows:
         assert abs(flops - 2 * avg) <= 2.0
+
+
+# ---------------------------------------------------------------- multi-model fusion
+
+def test_render_mean_of_constant_models(om):
+    """Eq. 11 on models whose experts are one constant colour c_h each: the
+    gates of a model sum to one, so model h renders exactly c_h wherever it
+    includes a kernel and 0 elsewhere, and the fused image is the mean of
+    those over all H models."""
+    rng = np.random.default_rng(60)
+    cols = [np.array([0.2, 0.4, 0.6]), np.array([0.9, 0.1, 0.5]), np.array([0.35, 0.8, 0.05])]
+    models = []
+    for h, c in enumerate(cols):
+        m = rand_model(om, rng, W=24, H=20, C=3, K=6 + 3 * h, linear=False, sig=(1.0, 2.5))
+        m.ea[:] = c
+        models.append(m)
+    y = om.render_mean(models)
+    expect = np.zeros((3, 20, 24))
+    covered_by = np.zeros((20, 24), int)
+    for m, c in zip(models, cols):
+        cov = om.render(m)[1] > 0
+        covered_by += cov
+        expect += c.astype(np.float32).astype(np.float64)[:, None, None] * cov   # FP32 experts
+    expect /= len(models)
+    assert np.any(covered_by < len(models))       # some pixels miss some models
+    assert np.any(covered_by == len(models))
+    np.testing.assert_allclose(y, expect, rtol=0, atol=1e-12)
+
+
+def test_render_mean_error_is_at_most_the_mean_model_error(om):
+    """Convexity of the squared error: the fused image's squared error to any
+    target is at most the mean of the models' squared errors (equal only
+    when the renders coincide), and fusing copies of one model, or one model
+    alone, returns its render; the order of the models does not matter."""
+    rng = np.random.default_rng(61)
+    models = [rand_model(om, rng, W=20, H=16, C=3, K=9, linear=True) for _ in range(4)]
+    t = rng.uniform(0, 1, (3, 16, 20))
+    y = om.render_mean(models)
+    singles = [om.render(m)[0] for m in models]
+    err_fused = np.sum((y - t) ** 2)
+    err_mean = np.mean([np.sum((s - t) ** 2) for s in singles])
+    assert err_fused < err_mean
+    np.testing.assert_allclose(om.render_mean(models[::-1]), y, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(om.render_mean([models[2]]), singles[2])
+    np.testing.assert_allclose(om.render_mean([models[1]] * 3), singles[1], rtol=0, atol=1e-15)
+
+
+def test_mm_denoise_fuses_fitted_models(om):
+    """The MM-RSMoE pipeline on a small noisy image: every model's loss goes
+    down and the fused image is the mean of the fitted models' renders."""
+    clean, noisy = synth.denoise_case(24, 16, 0.01, seed=62)
+    models = []
+    for h, off in enumerate([(0, 0), (4, 0), (0, 4), (4, 4)]):
+        p = synth.init_params(noisy, 12, 3.0, True, 62 + h, offset=off)
+        models.append(om.Model(24, 16, 3, p.mu, p.chol, p.ea, p.eW, tile=8))
+    y, losses = om.mm_denoise(models, noisy, 15, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))
+    for l in losses:
+        assert l[-1] < l[0]
+    np.testing.assert_allclose(y, np.mean([om.render(m)[0] for m in models], axis=0),
+                               rtol=0, atol=1e-14)
