@@ -506,6 +506,21 @@ def main():
     sr_ms = f0.elapsed_time(f1)
     sr_pairs = evaluated_pairs(sr.tile_off.cpu().numpy(), 2 * W, 2 * H, T)
 
+    # irregular-raster resampling at 10x magnification: a 205 x 205 crop of
+    # the current model on a jittered 10x raster (4.2 M points)
+    g10 = (np.arange(2050) + 0.5) / 10.0
+    pts = np.stack(np.meshgrid(900.0 + g10, 900.0 + g10), -1).reshape(-1, 2)
+    pts += np.random.default_rng(11).uniform(-0.04, 0.04, pts.shape)
+    pts = torch.tensor(pts, dtype=torch.float32, device="cuda")
+    rp = api.Rasterizer(desc, params.K, pair_cap=fb.pair_cap).bin(fb.params_of(0))
+    yp, ip = rp.render_points(pts)
+    torch.cuda.synchronize()
+    f0.record(stream)
+    rp.render_points(pts, yp, ip)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    pts_ms = f0.elapsed_time(f1)
+
     # job-wide aggregation (max time over ranks, summed work)
     vals = torch.tensor([tot_s, pairs_step * args.steps, e2e_s, sum(tile_ms) / 1e3],
                         dtype=torch.float64, device="cuda")
@@ -575,6 +590,9 @@ def main():
             "fit_iters_per_s": args.steps / tot_s,
             "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
                              "Gpairs_per_s": sr_pairs / sr_ms / 1e6},
+            "resample_points_10x": {"points": int(pts.shape[0]), "ms": pts_ms,
+                                    "Gpoints_per_s": pts.shape[0] / pts_ms / 1e6,
+                                    "raster": "jittered 10x raster over a 205x205 crop"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 8},

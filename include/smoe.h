@@ -78,7 +78,9 @@ typedef struct {
     int32_t C;        /* channels: 1 or 3 */
     int32_t tile;     /* tile side in pixels: 8, 16 or 32 (Sec. IV-C uses 16) */
     int32_t expert;   /* 0 = constant experts, 1 = linear experts */
-    float qmax;       /* truncation radius q_max (Mahalanobis, squared); 9 = 3 sigma */
+    float qmax;       /* truncation radius q_max (Mahalanobis, squared); 9 = 3 sigma;
+                         at most 174, so that exp(-q/2) of every included pair is a
+                         normal FP32 number (larger values: SMOE_ERR_ARG) */
     float scale;      /* resampling scale s >= 0: L' = L / s, eW' = eW / s; 1 for a fit */
 } smoe_desc;
 
@@ -247,6 +249,46 @@ SMOE_API smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_
 SMOE_API smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
                                           int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
                                           int32_t *status, void *stream);
+
+/* Native sharpening by kernel editing (Sec. II-B, Sec. VII-C): the kernel
+ * bandwidths divided by a sharpening factor f, i.e. L' = f L (P' = f^2 P):
+ * chol_out[i] = f * chol_in[i] for the 3K entries, each rounded to float
+ * once.  Render the edited model with q_max' = q_max * f * f (float
+ * products) so each kernel keeps the support of the fitted model and only
+ * the gates steepen (f > 1 sharpens edges; flat regions keep their value).
+ * q_max' must stay <= 174 (f <= 4.39 for q_max = 9): beyond it the gate of a
+ * far included pair leaves the FP32 range.
+ *   chol_in, chol_out: K x 3 FP32 (device); they may be the same buffer
+ *   factor: finite, > 0
+ * Returns SMOE_ERR_ARG for a bad K or factor. */
+SMOE_API smoe_status smoe_sharpen(const float *chol_in, float *chol_out, int64_t K,
+                                  float factor, void *stream);
+
+/* Bytes of the scratch that smoe_render_points needs for n_points points on
+ * the raster of d. */
+SMOE_API smoe_status smoe_points_workspace_size(const smoe_desc *d, int64_t n_points,
+                                                size_t *bytes);
+
+/* Resample the continuous regression function y(x) (Eqs. 3-5) at arbitrary
+ * sample points: super-resolution to any size on a regular or an irregular
+ * raster (Sec. II-B).  The model is the one smoe_bin(d, ...) prepared in ws
+ * with its lists tile_off / pair_k (any d->scale; the points are in the
+ * pixel units of d's W x H raster, pixel (i, j) having centre
+ * (i + 0.5, j + 0.5)).  Each point is evaluated with the same truncated model
+ * as smoe_render (FP32 predicate at the point's FP32 coordinates, kernels in
+ * ascending order); a point outside [0, W) x [0, H) or with a non-finite
+ * coordinate gets y = 0 and inv_d = 0.
+ *   K, ws, ws_bytes, tile_off, pair_k: as smoe_render
+ *   xy:   n_points x 2 FP32 (device, 8-byte aligned), (x, y) per point
+ *   pws:  scratch of smoe_points_workspace_size bytes (256-byte aligned)
+ *   y:    out, C x n_points FP32 (channel-planar); inv_d: out, n_points or NULL
+ *   status: the binning's status word; nothing is written if it is nonzero
+ * Returns SMOE_ERR_ARG / SMOE_ERR_WORKSPACE synchronously. */
+SMOE_API smoe_status smoe_render_points(const smoe_desc *d, int64_t K, const void *ws,
+                                        size_t ws_bytes, const int32_t *tile_off,
+                                        const int32_t *pair_k, int64_t n_points, const float *xy,
+                                        void *pws, size_t pws_bytes, float *y, float *inv_d,
+                                        const int32_t *status, void *stream);
 
 /* Bin and render one model without allocating anything: for callers that
  * cannot call cudaMalloc (a plugin inside an application that owns every

@@ -63,6 +63,8 @@ def _load():
         lib.om_bin.restype = I64
         lib.om_render.argtypes = [MP, I64, P, P, P, P]
         lib.om_render.restype = None
+        lib.om_render_points.argtypes = [MP, I64, P, P, P, P]
+        lib.om_render_points.restype = None
         lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P, P, P, P, P]
         lib.om_backward.restype = None
         lib.om_adam.argtypes = [I64, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -177,6 +179,35 @@ def render(m: Model, pixels=None, with_scale=False):
         y, invd = y.reshape(m.C, m.H, m.W), invd.reshape(m.H, m.W)
         absm = None if absm is None else absm.reshape(m.C, m.H, m.W)
     return (y, invd, absm) if with_scale else (y, invd)
+
+
+def render_points(m: Model, xy, with_scale=False):
+    """FP64 resampling of the model at arbitrary points (Sec. II-B): xy is
+    (n, 2) in the raster's pixel units (pixel (i, j) has centre (i+0.5,
+    j+0.5)), taken as float32; a point outside [0,W) x [0,H) gets 0.
+    Returns (y (C, n), invd (n,)) and, with with_scale, the term scale."""
+    lib = _load()
+    c = m._c()
+    pts = np.ascontiguousarray(xy, dtype=np.float32).reshape(-1, 2)
+    n = len(pts)
+    y = np.zeros((m.C, n), np.float64)
+    invd = np.zeros(n, np.float64)
+    absm = np.zeros((m.C, n), np.float64) if with_scale else None
+    lib.om_render_points(ctypes.byref(c), n, _ptr(pts), _ptr(y), _ptr(invd), _ptr(absm))
+    return (y, invd, absm) if with_scale else (y, invd)
+
+
+def sharpen(m: Model, f: float) -> Model:
+    """Native sharpening by kernel editing (Sec. II-B, Sec. VII-C): every
+    kernel's bandwidth divided by the sharpening factor f, i.e. L' = f L
+    (P' = f^2 P), each entry rounded to float once; the cutoff becomes
+    q_max' = q_max f^2 (float32 products), so the set of included points
+    stays that of the fitted model and only the gates get steeper."""
+    f32 = np.float32(f)
+    chol = (m.chol.astype(np.float32) * f32).astype(np.float32)
+    qmax = float(np.float32(m.qmax) * (f32 * f32))
+    return Model(m.W, m.H, m.C, m.mu.copy(), chol, m.ea.copy(),
+                 None if m.eW is None else m.eW.copy(), tile=m.tile, qmax=qmax, scale=m.scale)
 
 
 def render_mean(models, pixels=None, with_scale=False):

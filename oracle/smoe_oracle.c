@@ -71,11 +71,10 @@ static void kernel_px(const om_model *m, int64_t k, float *mx, float *my,
 /* Truncation predicate (Sec. IV, 99% / q_max ellipse), FP32, one rounding per
  * step:  dx = x0-mx, dy = y0-my, t = b*dy, z0 = fma(a,dx,t), z1 = c*dy,
  * q32 = fma(z0, z0, z1*z1);  included <=> q32 <= q_max. */
-int om_included(const om_model *m, int64_t k, int32_t i, int32_t j)
+static int included_at(const om_model *m, int64_t k, float x0, float y0)
 {
     float mx, my, a, b, c;
     kernel_px(m, k, &mx, &my, &a, &b, &c);
-    float x0 = (float)i + 0.5f, y0 = (float)j + 0.5f;
     float dx = x0 - mx;
     float dy = y0 - my;
     float t = b * dy;
@@ -84,6 +83,12 @@ int om_included(const om_model *m, int64_t k, int32_t i, int32_t j)
     float u = z1 * z1;
     float q32 = fmaf(z0, z0, u);
     return q32 <= m->qmax;
+}
+
+/* The predicate at the centre (i + 0.5, j + 0.5) of pixel (i, j). */
+int om_included(const om_model *m, int64_t k, int32_t i, int32_t j)
+{
+    return included_at(m, k, (float)i + 0.5f, (float)j + 0.5f);
 }
 
 /* Bounding box of kernel k as an inclusive tile rectangle (Sec. IV-B, the
@@ -188,13 +193,13 @@ int64_t om_bin(const om_model *m, int64_t n_sel, const int64_t *tiles,
  * defined as the float product mu_n * W); the rest is exact FP64. */
 typedef struct { double dx, dy, z0, z1, e; double mexp[3]; } om_pair;
 
-static void pair_value(const om_model *m, int64_t k, int32_t i, int32_t j,
-                       om_pair *pr)
+static void pair_value_at(const om_model *m, int64_t k, double x, double y,
+                          om_pair *pr)
 {
     float mx, my, a, b, c;
     kernel_px(m, k, &mx, &my, &a, &b, &c);
-    double dx = ((double)i + 0.5) - (double)mx;
-    double dy = ((double)j + 0.5) - (double)my;
+    double dx = x - (double)mx;
+    double dy = y - (double)my;
     double z0 = (double)a * dx + (double)b * dy;
     double z1 = (double)c * dy;
     double q = z0 * z0 + z1 * z1;
@@ -216,17 +221,24 @@ static void pair_value(const om_model *m, int64_t k, int32_t i, int32_t j,
     }
 }
 
-/* Gate denominator D and numerators N_c at one pixel over all K kernels;
- * A_c (if non-NULL) receives sum_k e_k |m_kc|, the scale of the sum. */
-static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
+static void pair_value(const om_model *m, int64_t k, int32_t i, int32_t j,
+                       om_pair *pr)
+{
+    pair_value_at(m, k, (double)i + 0.5, (double)j + 0.5, pr);
+}
+
+/* Gate denominator D and numerators N_c at the sample point (x, y) (FP32
+ * pixel units) over all K kernels; A_c (if non-NULL) receives
+ * sum_k e_k |m_kc|, the scale of the sum. */
+static void point_sums(const om_model *m, float x, float y, double *D,
                        double *N, double *A)
 {
     double d = 0.0;
     for (int ch = 0; ch < m->C; ++ch) { N[ch] = 0.0; if (A) A[ch] = 0.0; }
     for (int64_t k = 0; k < m->K; ++k) {
-        if (!om_included(m, k, i, j)) continue;
+        if (!included_at(m, k, x, y)) continue;
         om_pair pr;
-        pair_value(m, k, i, j, &pr);
+        pair_value_at(m, k, (double)x, (double)y, &pr);
         d += pr.e;
         for (int ch = 0; ch < m->C; ++ch) {
             N[ch] += pr.e * pr.mexp[ch];
@@ -234,6 +246,12 @@ static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
         }
     }
     *D = d;
+}
+
+static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
+                       double *N, double *A)
+{
+    point_sums(m, (float)i + 0.5f, (float)j + 0.5f, D, N, A);
 }
 
 /* Forward render (Eqs. 2-5): y_c = N_c / D, invd = 1/D; a pixel with no
@@ -252,6 +270,31 @@ void om_render(const om_model *m, int64_t n_px, const int64_t *px, double *y,
         int32_t i = (int32_t)(f % m->W), j = (int32_t)(f / m->W);
         double D, N[3], A[3];
         pixel_sums(m, i, j, &D, N, A);
+        for (int ch = 0; ch < m->C; ++ch) {
+            y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;
+            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / D : 0.0;
+        }
+        if (invd) invd[p] = D > 0.0 ? 1.0 / D : 0.0;
+    }
+}
+
+/* Resampling of the continuous regression function (Sec. II-B: "pixel
+ * interpolation to any size, with regular or irregular pixel raster"): y(x)
+ * at n sample points xy[2p], xy[2p+1] given in the raster's pixel units
+ * (pixel (i, j) has centre (i + 0.5, j + 0.5)).  The truncated model is the
+ * same pointwise definition as om_render (predicate in FP32 at the given
+ * coordinates, values in FP64).  A point outside [0, W) x [0, H), or with a
+ * non-finite coordinate, gets y = 0 and invd = 0.  Layout as om_render with
+ * the points in place of pixels. */
+void om_render_points(const om_model *m, int64_t n, const float *xy, double *y,
+                      double *invd, double *absm)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < n; ++p) {
+        float x = xy[2 * p], yy = xy[2 * p + 1];
+        double D = 0.0, N[3] = {0.0, 0.0, 0.0}, A[3] = {0.0, 0.0, 0.0};
+        if (x >= 0.0f && x < (float)m->W && yy >= 0.0f && yy < (float)m->H)
+            point_sums(m, x, yy, &D, N, A);
         for (int ch = 0; ch < m->C; ++ch) {
             y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;
             if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / D : 0.0;

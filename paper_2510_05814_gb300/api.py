@@ -209,17 +209,74 @@ class Rasterizer:
                              target, grad, self.status, stream)
         return grad
 
+    def render_points(self, xy, y=None, inv_d=None, stream=None):
+        """y(x) at the (n, 2) float32 CUDA points ``xy`` (pixel units of this
+        raster); returns (y (C, n), inv_d (n,))."""
+        d = self.desc
+        xy = xy.contiguous()
+        assert xy.dtype == torch.float32 and xy.dim() == 2 and xy.shape[1] == 2
+        n = xy.shape[0]
+        if y is None:
+            y = torch.empty(d.C, n, dtype=torch.float32, device=self.device)
+        if inv_d is None:
+            inv_d = torch.empty(n, dtype=torch.float32, device=self.device)
+        lib = _lib.load()
+        nb = ctypes.c_size_t(0)
+        check(lib.smoe_points_workspace_size(ctypes.byref(d.c()), n, ctypes.byref(nb)),
+              "smoe_points_workspace_size")
+        if getattr(self, "_pws", None) is None or self._pws.numel() < nb.value:
+            raw = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+            off = (-raw.data_ptr()) % 256
+            self._pws = raw[off:off + nb.value]
+        check(lib.smoe_render_points(ctypes.byref(d.c()), self.K, _ptr(self.ws), self.ws.numel(),
+                                     _ptr(self.tile_off), _ptr(self.pair_k), n, _ptr(xy),
+                                     _ptr(self._pws), self._pws.numel(), _ptr(y), _ptr(inv_d),
+                                     _ptr(self.status), _stream(stream)), "smoe_render_points")
+        return y, inv_d
+
     def lists(self):
         """(tile_off, pair_k) trimmed to the pair count, on the host."""
         off = self.tile_off.cpu().numpy()
         return off, self.pair_k[: int(off[-1])].cpu().numpy()
 
 
-def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0):
-    """Bin and render ``params`` on a W x H raster; returns (y, inv_d, rasterizer)."""
+def sharpen(params: SMoEParams, factor: float, qmax: float = 9.0):
+    """Native sharpening by kernel editing (Sec. II-B): a model whose kernel
+    bandwidths are divided by ``factor`` (L' = factor L, on the GPU; mu and
+    the experts are shared with ``params``) and the cutoff that keeps each
+    kernel's support, q_max' = q_max factor^2 (float32 products).  Returns
+    (sharpened params, q_max')."""
+    f32 = np.float32(factor)
+    qmax2 = float(np.float32(qmax) * (f32 * f32))
+    if not qmax2 <= 174.0:
+        raise ValueError(f"sharpening {factor} x at q_max {qmax} needs q_max' = {qmax2} > 174, "
+                         "beyond the FP32 range of the gates")
+    chol = torch.empty_like(params.chol)
+    check(_lib.load().smoe_sharpen(_ptr(params.chol), _ptr(chol), params.K, float(factor),
+                                   _stream(None)), "smoe_sharpen")
+    return SMoEParams(params.mu, chol, params.ea, params.eW), qmax2
+
+
+def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0, sharpen_factor=None):
+    """Bin and render ``params`` on a W x H raster (``scale`` times the fitted
+    raster, optionally sharpened); returns (y, inv_d, rasterizer)."""
+    if sharpen_factor is not None and sharpen_factor != 1.0:
+        params, qmax = sharpen(params, sharpen_factor, qmax)
     desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, scale)
     r = Rasterizer(desc, params.K).bin(params)
     y, inv_d = r.render()
+    return y, inv_d, r
+
+
+def render_points(params: SMoEParams, W, H, xy, tile=16, qmax=9.0, sharpen_factor=None):
+    """Resample the model fitted on a W x H raster at the (n, 2) points
+    ``xy`` (pixel units of that raster): super-resolution on an irregular
+    raster.  Returns (y (C, n), inv_d (n,), rasterizer)."""
+    if sharpen_factor is not None and sharpen_factor != 1.0:
+        params, qmax = sharpen(params, sharpen_factor, qmax)
+    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, 1.0)
+    r = Rasterizer(desc, params.K).bin(params)
+    y, inv_d = r.render_points(xy)
     return y, inv_d, r
 
 

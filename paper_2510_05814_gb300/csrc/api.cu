@@ -12,6 +12,9 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int64_t kMaxTiles = 4096LL * 4096LL;   // prefix-sum capacity (4096 chunks)
+// Largest cutoff: exp(-q/2) of an included pair stays an FP32 normal number
+// (q log2(e) / 2 <= 125.5), so no included kernel is flushed to zero.
+constexpr float kMaxQmax = 174.0f;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -62,7 +65,7 @@ bool desc_ok(const smoe_desc *d) {
     if (d->C != 1 && d->C != 3) return false;
     if (d->tile != 8 && d->tile != 16 && d->tile != 32) return false;
     if (d->expert != 0 && d->expert != 1) return false;
-    if (!(d->qmax > 0.0f) || std::isnan(d->qmax)) return false;
+    if (!(d->qmax > 0.0f) || !(d->qmax <= kMaxQmax)) return false;
     if (!(d->scale > 0.0f) || !std::isfinite(d->scale)) return false;
     if (tiles_of(d->W, d->H, d->tile) > kMaxTiles) return false;
     return true;
@@ -129,7 +132,7 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
     if (bt->C != 1 && bt->C != 3) return false;
     if (bt->tile != 8 && bt->tile != 16 && bt->tile != 32) return false;
     if (bt->expert != 0 && bt->expert != 1) return false;
-    if (!(bt->qmax > 0.0f) || !bt->step) return false;
+    if (!(bt->qmax > 0.0f) || !(bt->qmax <= kMaxQmax) || !bt->step) return false;
     if (bt->loss && bt->hist <= 0) return false;
     int64_t K_total = 0, t_total = 0;
     tab->resize(bt->B);
@@ -415,6 +418,71 @@ smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_ima
     cudaError_t e = launch_bin(g, w, st);
     if (e == cudaSuccess) e = launch_render_mean(g, w, y, st);
     return cuda_status(e);
+}
+
+smoe_status smoe_sharpen(const float *chol_in, float *chol_out, int64_t K, float factor,
+                         void *stream) {
+    if (K < 0 || K > 0x7fffffffLL || !(factor > 0.0f) || !std::isfinite(factor) ||
+        (K > 0 && (!chol_in || !chol_out)))
+        return SMOE_ERR_ARG;
+    return cuda_status(launch_scale(chol_in, chol_out, 3 * K, factor,
+                                    static_cast<cudaStream_t>(stream)));
+}
+
+// Points scratch: cnt, cursor, off (tiles + 1), bsum, n_in, n_long, pt_tile, order.
+struct PointLayout {
+    size_t cnt, cursor, off, bsum, n_in, n_long, pt_tile, order, total;
+};
+
+static PointLayout point_layout(int64_t tiles, int64_t n) {
+    PointLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+    L.cnt = take(sizeof(int32_t) * (size_t)tiles);
+    L.cursor = take(sizeof(int32_t) * (size_t)tiles);
+    L.off = take(sizeof(int32_t) * (size_t)(tiles + 1));
+    L.bsum = take(sizeof(long long) * (size_t)scan_blocks_of(tiles));
+    L.n_in = take(sizeof(int64_t));
+    L.n_long = take(sizeof(int32_t));
+    L.pt_tile = take(sizeof(int32_t) * (size_t)n);
+    L.order = take(sizeof(int32_t) * (size_t)n);
+    L.total = o;
+    return L;
+}
+
+smoe_status smoe_points_workspace_size(const smoe_desc *d, int64_t n_points, size_t *bytes) {
+    if (!desc_ok(d) || n_points < 0 || n_points > 0x7fffffffLL || !bytes) return SMOE_ERR_ARG;
+    *bytes = point_layout(tiles_of(d->W, d->H, d->tile), n_points).total;
+    return SMOE_OK;
+}
+
+smoe_status smoe_render_points(const smoe_desc *d, int64_t K, const void *ws, size_t ws_bytes,
+                               const int32_t *tile_off, const int32_t *pair_k, int64_t n_points,
+                               const float *xy, void *pws, size_t pws_bytes, float *y,
+                               float *inv_d, const int32_t *status, void *stream) {
+    if (!desc_ok(d) || K < 0 || K > 0x7fffffffLL || !tile_off || n_points < 0 ||
+        n_points > 0x7fffffffLL)
+        return SMOE_ERR_ARG;
+    if (n_points > 0 && (!xy || !y || (reinterpret_cast<uintptr_t>(xy) & 7) != 0))
+        return SMOE_ERR_ARG;
+    Geo g = make_geo(d, K);
+    const Layout L = layout(K, g.tiles_total, 0, g.S, g.GS, 1, false);
+    if (!ws_ok(ws, ws_bytes, L.total)) return SMOE_ERR_WORKSPACE;
+    const PointLayout PL = point_layout(g.tiles_total, n_points);
+    if (!ws_ok(pws, pws_bytes, PL.total)) return SMOE_ERR_WORKSPACE;
+    char *b = static_cast<char *>(pws);
+    PointBufs pb{};
+    pb.cnt = reinterpret_cast<int32_t *>(b + PL.cnt);
+    pb.cursor = reinterpret_cast<int32_t *>(b + PL.cursor);
+    pb.off = reinterpret_cast<int32_t *>(b + PL.off);
+    pb.bsum = reinterpret_cast<long long *>(b + PL.bsum);
+    pb.n_in = reinterpret_cast<int64_t *>(b + PL.n_in);
+    pb.n_long = reinterpret_cast<int32_t *>(b + PL.n_long);
+    pb.pt_tile = reinterpret_cast<int32_t *>(b + PL.pt_tile);
+    pb.order = reinterpret_cast<int32_t *>(b + PL.order);
+    const float *rec = reinterpret_cast<const float *>(static_cast<const char *>(ws) + L.rec);
+    return cuda_status(launch_render_points(g, rec, tile_off, pair_k, n_points, xy, pb, y, inv_d,
+                                            status, static_cast<cudaStream_t>(stream)));
 }
 
 smoe_status smoe_get_status(const int32_t *status, void *stream) {

@@ -436,4 +436,14 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
 
 int64_t scan_blocks(int64_t n_tiles) { return (n_tiles + kScanChunk - 1) / kScanChunk; }
 
+cudaError_t launch_exscan(int64_t n, const int32_t *cnt, long long *bsum, int32_t *off,
+                          int64_t *total, int32_t *n_long, int32_t *cursor, int64_t cap,
+                          int32_t *status, cudaStream_t st) {
+    const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(n, cnt, bsum, status);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(nb, bsum, n, off, total, n_long, cap, status);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(n, cnt, bsum, off, cursor, cap, status);
+    return cudaGetLastError();
+}
+
 }  // namespace smoe

@@ -1,0 +1,164 @@
+// Resampling and kernel editing (Sec. II-B, Sec. VII-C):
+//   - smoe_sharpen: native sharpening, L' = f L (bandwidths divided by f);
+//   - smoe_render_points: the continuous regression function y(x) (Eq. 5)
+//     at arbitrary sample points, i.e. super-resolution on a regular or an
+//     irregular raster.
+//
+// Points: each in-image point gets the tile of the model raster it lies in;
+// a counting sort by tile (count, the binning's prefix sum, scatter) puts
+// the points of one tile next to each other, and one thread per point then
+// walks its tile's kernel list.  Neighbouring threads of a warp mostly share
+// a tile, so their reads of a kernel's prepared record are the same address
+// (one transaction for the warp) and the records stay in L2.
+#include <cmath>
+
+#include "smoe_internal.cuh"
+
+namespace smoe {
+
+namespace {
+
+constexpr int kPtThreads = 256;
+
+__global__ void k_scale(const float *__restrict__ in, float *__restrict__ out, int64_t n,
+                        float f) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __fmul_rn(in[i], f);
+}
+
+// Tile of each point (-1 outside [0,W) x [0,H) or non-finite; such a point's
+// outputs are written as 0 here) and the per-tile counts.
+__global__ void k_pt_tile(int64_t n, const float2 *__restrict__ xy, int W, int H, int T,
+                          int tiles_x, int C, int32_t *__restrict__ pt_tile,
+                          int32_t *__restrict__ cnt, float *__restrict__ y,
+                          float *__restrict__ inv_d, const int32_t *status) {
+    if (status_bad(status)) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float2 p = xy[i];
+    int32_t t = -1;
+    if (p.x >= 0.0f && p.x < (float)W && p.y >= 0.0f && p.y < (float)H) {
+        // floor of a float in [0, W): exact integer conversion
+        const int tx = min((int)p.x / T, tiles_x - 1);
+        const int ty = (int)p.y / T;
+        t = ty * tiles_x + tx;
+        atomicAdd(&cnt[t], 1);
+    } else {
+        for (int ch = 0; ch < C; ++ch) y[ch * n + i] = 0.0f;
+        if (inv_d) inv_d[i] = 0.0f;
+    }
+    pt_tile[i] = t;
+}
+
+__global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
+                             const int32_t *__restrict__ off, int32_t *__restrict__ cursor,
+                             int32_t *__restrict__ order, const int32_t *status) {
+    if (status_bad(status)) return;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t t = pt_tile[i];
+    if (t < 0) return;
+    order[off[t] + atomicAdd(&cursor[t], 1)] = (int32_t)i;
+}
+
+// One thread per sorted in-image point: D = sum e_k, N_c = sum e_k m_kc over
+// the tile's list in ascending kernel order, y_c = N_c / D (0 where D = 0).
+template <int C, bool LIN>
+__global__ void __launch_bounds__(kPtThreads) k_render_points(
+    int64_t n, const int64_t *__restrict__ n_in, const float2 *__restrict__ xy,
+    const int32_t *__restrict__ order, const int32_t *__restrict__ pt_tile,
+    const int32_t *__restrict__ tile_off, const int32_t *__restrict__ pair_k,
+    const float *__restrict__ rec, int S, float qmax, float *__restrict__ y,
+    float *__restrict__ inv_d, const int32_t *status) {
+    constexpr int E = LIN ? 3 : 1;
+    if (status_bad(status)) return;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= *n_in) return;
+    const int32_t i = order[j];
+    const int32_t t = pt_tile[i];
+    const float2 p = xy[i];
+    float D = 0.0f, N[C];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) N[ch] = 0.0f;
+    const int32_t e = tile_off[t + 1];
+    for (int32_t q = tile_off[t]; q < e; ++q) {
+        const float *r = rec + (int64_t)pair_k[q] * S;
+        const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
+        const float c = __ldg(r + 4);
+        const float dx = __fsub_rn(p.x, r0.x);
+        const float dy = __fsub_rn(p.y, r0.y);
+        const float tb = __fmul_rn(r0.w, dy);
+        const float z1 = __fmul_rn(c, dy);
+        const float u = __fmul_rn(z1, z1);
+        float z0;
+        const float qv = q_of(r0.z, dx, tb, u, z0);
+        if (!(qv <= qmax)) continue;
+        const float ev = ex2(__fmul_rn(qv, kNegHalfLog2e));
+        D += ev;
+#pragma unroll
+        for (int ch = 0; ch < C; ++ch) {
+            float m = __ldg(r + 7 + ch * E);
+            if (LIN) m = __fmaf_rn(__ldg(r + 7 + ch * E + 1), dx,
+                                   __fmaf_rn(__ldg(r + 7 + ch * E + 2), dy, m));
+            N[ch] = __fmaf_rn(ev, m, N[ch]);
+        }
+    }
+    const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) y[ch * n + i] = N[ch] * inv;
+    if (inv_d) inv_d[i] = inv;
+}
+
+template <int C, bool LIN>
+void launch_points_kernel(unsigned grid, cudaStream_t st, int64_t n, const int64_t *n_in,
+                          const float2 *xy, const int32_t *order, const int32_t *pt_tile,
+                          const int32_t *tile_off, const int32_t *pair_k, const float *rec,
+                          int S, float qmax, float *y, float *inv_d, const int32_t *status) {
+    k_render_points<C, LIN><<<grid, kPtThreads, 0, st>>>(n, n_in, xy, order, pt_tile, tile_off,
+                                                         pair_k, rec, S, qmax, y, inv_d, status);
+}
+
+}  // namespace
+
+cudaError_t launch_scale(const float *in, float *out, int64_t n, float f, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = (n + 255) / 256;
+    k_scale<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(in, out, n, f);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_points(const Geo &g, const float *rec, const int32_t *tile_off,
+                                 const int32_t *pair_k, int64_t n, const float *xy,
+                                 const PointBufs &pb, float *y, float *inv_d,
+                                 const int32_t *status, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t tiles = g.tiles_total;
+    cudaError_t e = cudaMemsetAsync(pb.cnt, 0, sizeof(int32_t) * tiles, st);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((n + kPtThreads - 1) / kPtThreads);
+    const float2 *p2 = reinterpret_cast<const float2 *>(xy);
+    k_pt_tile<<<grid, kPtThreads, 0, st>>>(n, p2, g.one.W, g.one.H, g.T, g.one.tiles_x, g.C,
+                                           pb.pt_tile, pb.cnt, y, inv_d, status);
+    // the points counted never exceed n: no capacity error is possible
+    e = launch_exscan(tiles, pb.cnt, pb.bsum, pb.off, pb.n_in, pb.n_long, pb.cursor, n,
+                      const_cast<int32_t *>(status), st);
+    if (e != cudaSuccess) return e;
+    k_pt_scatter<<<grid, kPtThreads, 0, st>>>(n, pb.pt_tile, pb.off, pb.cursor, pb.order, status);
+    const int S = g.S;
+    if (g.C == 1 && !g.linear)
+        launch_points_kernel<1, false>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
+                                       pair_k, rec, S, g.qmax, y, inv_d, status);
+    else if (g.C == 1)
+        launch_points_kernel<1, true>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
+                                      pair_k, rec, S, g.qmax, y, inv_d, status);
+    else if (!g.linear)
+        launch_points_kernel<3, false>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
+                                       pair_k, rec, S, g.qmax, y, inv_d, status);
+    else
+        launch_points_kernel<3, true>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
+                                      pair_k, rec, S, g.qmax, y, inv_d, status);
+    return cudaGetLastError();
+}
+
+}  // namespace smoe

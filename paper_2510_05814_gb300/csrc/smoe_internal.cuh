@@ -152,6 +152,28 @@ __device__ __forceinline__ bool status_bad(const int32_t *status) {
 cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st);
 cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
                           cudaStream_t st);
+// Exclusive prefix sum of n counters into off[0..n] (off[n] = min(total, cap),
+// *total = the sum, cursor[0..n) zeroed; a total above cap sets
+// SMOE_ERR_CAPACITY); needs scan_blocks(n) entries of bsum.
+cudaError_t launch_exscan(int64_t n, const int32_t *cnt, long long *bsum, int32_t *off,
+                          int64_t *total, int32_t *n_long, int32_t *cursor, int64_t cap,
+                          int32_t *status, cudaStream_t st);
+int64_t scan_blocks(int64_t n_tiles);
+// Scratch of smoe_render_points: per-tile counts / cursors / offsets of the
+// points, prefix-sum block sums, each point's tile and the tile-sorted order.
+struct PointBufs {
+    int32_t *cnt, *cursor, *off, *pt_tile, *order, *n_long;
+    long long *bsum;
+    int64_t *n_in;
+};
+// out = f * in elementwise (one rounding), n floats.
+cudaError_t launch_scale(const float *in, float *out, int64_t n, float f, cudaStream_t st);
+// y(x) of one model (g.B == 1) at n points xy (n x 2, pixel units of g.one's
+// raster) from the model's prepared records and tile lists.
+cudaError_t launch_render_points(const Geo &g, const float *rec, const int32_t *tile_off,
+                                 const int32_t *pair_k, int64_t n, const float *xy,
+                                 const PointBufs &pb, float *y, float *inv_d,
+                                 const int32_t *status, cudaStream_t st);
 // Mean of the renders of a batch's B models (all images one size), Eq. 11.
 cudaError_t launch_render_mean(const Geo &g, const Bufs &w, float *y, cudaStream_t st);
 cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const float *inv_d,

@@ -599,3 +599,132 @@ def test_mm_denoise_fuses_fitted_models(om):
         assert l[-1] < l[0]
     np.testing.assert_allclose(y, np.mean([om.render(m)[0] for m in models], axis=0),
                                rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- resampling and sharpening
+
+def qxy(m, k, x, y):
+    """FP64 quadratic form of kernel k at the point (x, y) (numpy matmul)."""
+    c, P = kernel_px64(m, k)
+    d = np.array([x, y], np.float64) - c
+    return float(d @ P @ d)
+
+
+def test_points_at_pixel_centres_equal_render(om):
+    rng = np.random.default_rng(70)
+    m = rand_model(om, rng, W=26, H=19, C=3, K=14, linear=True)
+    y, invd = om.render(m)
+    xs = np.stack(np.meshgrid(np.arange(26) + 0.5, np.arange(19) + 0.5), -1).reshape(-1, 2)
+    yp, ip = om.render_points(m, xs)
+    np.testing.assert_array_equal(yp, y.reshape(3, -1))
+    np.testing.assert_array_equal(ip, invd.reshape(-1))
+
+
+def test_points_single_kernel_closed_form(om):
+    """One kernel with a linear expert evaluated at random continuous points:
+    y = ea + eW (x - mu) where the point is inside the cutoff (numpy FP64
+    quadratic form), 0 outside; 1/D = exp(q/2).  Catches an x/y swap of the
+    point coordinates or of the slopes."""
+    m = om.Model(30, 22, 3, np.array([[0.37, 0.58]]), np.array([[0.23, -0.09, 0.17]]),
+                 np.array([[0.2, 0.5, 0.9]]),
+                 np.array([[[0.02, -0.03], [0.05, 0.01], [-0.01, 0.025]]]))
+    rng = np.random.default_rng(71)
+    pts = rng.uniform([0, 0], [30, 22], (400, 2)).astype(np.float32)
+    y, invd = om.render_points(m, pts)
+    c, _ = kernel_px64(m, 0)
+    n_in = 0
+    for p in range(len(pts)):
+        q = qxy(m, 0, pts[p, 0], pts[p, 1])
+        if abs(q - 9.0) < 1e-4:
+            continue
+        if q < 9.0:
+            n_in += 1
+            d = pts[p].astype(np.float64) - c
+            np.testing.assert_allclose(y[:, p], m.ea[0] + m.eW[0].astype(np.float64) @ d,
+                                       rtol=1e-13, atol=1e-15)
+            assert invd[p] == pytest.approx(math.exp(0.5 * q), rel=1e-10)
+        else:
+            assert np.all(y[:, p] == 0) and invd[p] == 0
+    assert n_in > 40
+
+
+def test_points_outside_the_raster_are_zero(om):
+    rng = np.random.default_rng(72)
+    m = rand_model(om, rng, W=16, H=12, C=1, K=6, linear=False, sig=(6.0, 9.0))
+    pts = np.array([[-0.01, 3.0], [16.0, 3.0], [3.0, 12.0], [3.0, -1e-6], [np.nan, 2.0],
+                    [2.0, np.inf], [15.999, 11.999], [0.0, 0.0]], np.float32)
+    y, invd = om.render_points(m, pts)
+    assert np.all(y[:, :6] == 0) and np.all(invd[:6] == 0)
+    assert np.all(invd[6:] > 0)
+
+
+@pytest.mark.parametrize("f", [1.0, 1.7, 3.0])
+def test_sharpen_two_kernel_logistic_closed_form(om, f):
+    """Sharpening by f (L' = f L) turns the two-kernel gate into a logistic in
+    f^2 (q2 - q1) / 2 with q from the unedited kernels; with q_max' = f^2 q_max
+    every pixel included before stays included."""
+    m = om.Model(32, 16, 1, np.array([[0.35, 0.5], [0.6, 0.45]]),
+                 np.array([[0.2, 0.05, 0.18], [0.15, -0.04, 0.22]]), np.array([[0.1], [0.9]]))
+    s = om.sharpen(m, f)
+    y, _ = om.render(s)
+    m1, m2 = float(np.float32(0.1)), float(np.float32(0.9))
+    n = 0
+    for j in range(m.H):
+        for i in range(m.W):
+            if om.included(m, 0, i, j) and om.included(m, 1, i, j):
+                n += 1
+                q1, q2 = q64(m, 0, i, j), q64(m, 1, i, j)
+                ref = m2 + (m1 - m2) * scipy.special.expit(0.5 * f * f * (q2 - q1))
+                # the edited L is rounded to float: relative error ~1e-7 in q
+                assert y[0, j, i] == pytest.approx(ref, abs=1e-5 * max(1.0, f * f * abs(q2 - q1)))
+    assert n > 50
+
+
+def test_sharpen_keeps_the_support_and_flat_regions(om):
+    """With q_max' = f^2 q_max the included (pixel, kernel) pairs are those of
+    the fitted model (up to float rounding at the boundary), so equal
+    constant experts still give a constant image wherever the model covered
+    it (Sec. II-B: flat regions are preserved)."""
+    rng = np.random.default_rng(73)
+    m = rand_model(om, rng, W=36, H=28, C=3, K=16, linear=False, sig=(1.5, 4.0))
+    s = om.sharpen(m, 2.5)
+    same = total = 0
+    for k in range(m.K):
+        for j in range(m.H):
+            for i in range(m.W):
+                a, b = om.included(m, k, i, j), om.included(s, k, i, j)
+                total += a or b
+                same += a == b and a
+    assert total > 500 and same >= total - 2
+    v = np.array([0.3, 0.6, 0.9], np.float32)
+    s.ea[:] = v
+    y, invd = om.render(s)
+    cov = invd > 0
+    for ch in range(3):
+        np.testing.assert_allclose(y[ch][cov], v[ch], rtol=1e-13)
+
+
+def test_sharpen_large_factor_tends_to_hard_assignment(om):
+    """As f grows the softmax gates tend to the indicator of the kernel with
+    the smallest q (Mahalanobis-nearest): for every covered pixel
+    |y - m_min| <= sum_{k != min} exp(-f^2 (q_k - q_min) / 2) |m_k - m_min|
+    (the gate of k is at most e_k / e_min), which f = 4 makes tiny at most
+    pixels.  (f^2 q_max = 144 keeps every included e_k inside the FP32 normal
+    range, the limit the library enforces.)"""
+    rng = np.random.default_rng(74)
+    m = rand_model(om, rng, W=30, H=24, C=1, K=10, linear=False, sig=(3.0, 6.0))
+    f = 4.0
+    y, _ = om.render(om.sharpen(m, f))
+    n_hard = 0
+    for j in range(m.H):
+        for i in range(m.W):
+            ks = [k for k in range(m.K) if om.included(m, k, i, j)]
+            if len(ks) < 2:
+                continue
+            q = sorted((q64(m, k, i, j), k) for k in ks)
+            mmin = float(m.ea[q[0][1], 0])
+            bound = sum(math.exp(-0.5 * f * f * (qk - q[0][0])) * abs(float(m.ea[k, 0]) - mmin)
+                        for qk, k in q[1:])
+            assert abs(y[0, j, i] - mmin) <= bound * (1 + 1e-6) + 1e-6
+            n_hard += bound < 1e-3
+    assert n_hard > 100
