@@ -159,16 +159,40 @@ def oracle_sample(wl, size):
     return pairs, time.perf_counter() - t0, om.threads(), int(p.mu.shape[0])
 
 
-def dist_init():
+def dist_init(backend="nccl"):
+    """Rank layout from the torchrun environment; joins the process group
+    when WORLD_SIZE > 1 (NCCL on GPUs; gloo for the CPU tests of this logic)."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return ws, rank, local
+
+
+def replica_seed(rank):
+    """Each rank fits its own image (independent problems, weak scaling)."""
+    return 3 + rank
+
+
+def aggregate(step_s, work, e2e_s, world, device="cuda"):
+    """Job-wide figures: the slowest rank's times (max) and the work of all
+    ranks (sum); the only collective of the benchmark, outside the timed
+    region."""
+    import torch
+    vals = torch.tensor([step_s, work, e2e_s], dtype=torch.float64, device=device)
+    if world == 1:
+        return float(vals[0]), float(vals[1]), float(vals[2])
+    mx, sm = vals.clone(), vals.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2])
 
 
 def run_reference(args):
@@ -423,7 +447,7 @@ def main():
     from paper_2510_05814_gb300 import api
     from paper_2510_05814_gb300.fit import FitBatch
 
-    wl = synth.rgb_2048(seed=3 + rank)
+    wl = synth.rgb_2048(seed=replica_seed(rank))
     C, H, W = wl.target.shape
     T = wl.tile
     tgt = torch.tensor(wl.target, device="cuda")
@@ -522,16 +546,7 @@ def main():
     pts_ms = f0.elapsed_time(f1)
 
     # job-wide aggregation (max time over ranks, summed work)
-    vals = torch.tensor([tot_s, pairs_step * args.steps, e2e_s, sum(tile_ms) / 1e3],
-                        dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = vals.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm_ = vals.clone()
-        torch.distributed.all_reduce(sm_, op=torch.distributed.ReduceOp.SUM)
-        tot_s, work, e2e_s = float(mx[0]), float(sm_[1]), float(mx[2])
-    else:
-        work = pairs_step * args.steps
+    tot_s, work, e2e_s = aggregate(tot_s, pairs_step * args.steps, e2e_s, world)
     value = work / tot_s / 1e9
     e2e_value = work / e2e_s / 1e9
 
