@@ -43,7 +43,8 @@ class _Model(ctypes.Structure):
                 ("qmax", ctypes.c_float), ("scale", ctypes.c_float),
                 ("K", ctypes.c_int64),
                 ("mu", ctypes.c_void_p), ("chol", ctypes.c_void_p),
-                ("ea", ctypes.c_void_p), ("eW", ctypes.c_void_p)]
+                ("ea", ctypes.c_void_p), ("eW", ctypes.c_void_p),
+                ("rbf", ctypes.c_int32), ("logpi", ctypes.c_void_p)]
 
 
 def _load():
@@ -65,7 +66,7 @@ def _load():
         lib.om_render.restype = None
         lib.om_render_points.argtypes = [MP, I64, P, P, P, P]
         lib.om_render_points.restype = None
-        lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P, P, P, P, P]
+        lib.om_backward.argtypes = [MP, P, P, I64, P, P, P, P, P, P, P, P, P, P, P]
         lib.om_backward.restype = None
         lib.om_adam.argtypes = [I64, P, P, P, P, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_int32]
@@ -74,7 +75,7 @@ def _load():
                                  ctypes.c_int32]
         lib.om_lr_mu.restype = ctypes.c_double
         lib.om_fit.argtypes = [MP, P, ctypes.c_int32, P, ctypes.c_double, ctypes.c_double,
-                               ctypes.c_double, P, P, P, P, P]
+                               ctypes.c_double, P, P, P, P, P, P]
         lib.om_fit.restype = None
         lib.om_threads.argtypes = []
         lib.om_threads.restype = ctypes.c_int32
@@ -93,7 +94,9 @@ class Model:
     mu (K,2) normalised, chol (K,3) = (a,b,c) of L = [[a,0],[b,c]] with
     precision P = L L^T in pixel units of the fitted raster, ea (K,C),
     eW (K,C,2) or None for constant experts.  ``scale`` resamples the model on
-    a raster ``scale`` times finer (L and eW divided by it)."""
+    a raster ``scale`` times finer (L and eW divided by it).  ``logpi`` (K,)
+    holds the gate weights log pi_k of Eq. 4 (None: pi = 1); ``rbf`` selects
+    the unnormalised RBF / Gaussian-splatting sum of Eq. 1 (D = 1)."""
     W: int
     H: int
     C: int
@@ -104,6 +107,8 @@ class Model:
     tile: int = 16
     qmax: float = 9.0
     scale: float = 1.0
+    logpi: np.ndarray | None = None
+    rbf: bool = False
 
     def __post_init__(self):
         f32 = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
@@ -112,6 +117,8 @@ class Model:
         self.ea = f32(self.ea).reshape(-1, self.C)
         if self.eW is not None:
             self.eW = f32(self.eW).reshape(-1, self.C, 2)
+        if self.logpi is not None:
+            self.logpi = f32(self.logpi).reshape(-1)
 
     @property
     def K(self) -> int:
@@ -122,10 +129,11 @@ class Model:
         return self.eW is not None
 
     def _c(self) -> _Model:
-        self._keep = (self.mu, self.chol, self.ea, self.eW)
+        self._keep = (self.mu, self.chol, self.ea, self.eW, self.logpi)
         return _Model(self.W, self.H, self.C, self.tile, int(self.linear),
                       float(self.qmax), float(self.scale), self.K,
-                      _ptr(self.mu), _ptr(self.chol), _ptr(self.ea), _ptr(self.eW))
+                      _ptr(self.mu), _ptr(self.chol), _ptr(self.ea), _ptr(self.eW),
+                      int(self.rbf), _ptr(self.logpi))
 
 
 def threads() -> int:
@@ -207,7 +215,8 @@ def sharpen(m: Model, f: float) -> Model:
     chol = (m.chol.astype(np.float32) * f32).astype(np.float32)
     qmax = float(np.float32(m.qmax) * (f32 * f32))
     return Model(m.W, m.H, m.C, m.mu.copy(), chol, m.ea.copy(),
-                 None if m.eW is None else m.eW.copy(), tile=m.tile, qmax=qmax, scale=m.scale)
+                 None if m.eW is None else m.eW.copy(), tile=m.tile, qmax=qmax, scale=m.scale,
+                 logpi=None if m.logpi is None else m.logpi.copy(), rbf=m.rbf)
 
 
 def render_mean(models, pixels=None, with_scale=False):
@@ -232,7 +241,8 @@ def mm_denoise(models, noisy, n_it, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3)):
 
 
 def backward(m: Model, gy=None, target=None, kernels=None, with_scale=False):
-    """FP64 gradient of the loss w.r.t. (mu, chol, ea, eW) in API units.
+    """FP64 gradient of the loss w.r.t. (mu, chol, ea, eW) in API units, and
+    w.r.t. logpi as a fifth entry when the model has gate weights.
 
     gy: upstream dL/dy (C,H,W) float64, or target (C,H,W) for the fused MSE
     loss sum((y-t)^2)/(C H W).  kernels: optional list of kernel ids.
@@ -245,15 +255,18 @@ def backward(m: Model, gy=None, target=None, kernels=None, with_scale=False):
 
     def alloc():
         return [np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, m.C)),
-                np.zeros((n, m.C, 2)) if m.linear else None]
-    g, sc = alloc(), (alloc() if with_scale else [None] * 4)
+                np.zeros((n, m.C, 2)) if m.linear else None,
+                np.zeros(n) if m.logpi is not None else None]
+    g, sc = alloc(), (alloc() if with_scale else [None] * 5)
     gy_ = None if gy is None else np.ascontiguousarray(gy, dtype=np.float64)
     t_ = None if target is None else np.ascontiguousarray(target, dtype=np.float32)
     if gy_ is None and t_ is None:
         raise ValueError("need gy or target")
     lib.om_backward(ctypes.byref(c), _ptr(gy_), _ptr(t_), 0 if sel is None else n, _ptr(sel),
-                    *[_ptr(x) for x in g], *[_ptr(x) for x in sc])
-    return (tuple(g), tuple(sc)) if with_scale else tuple(g)
+                    *[_ptr(x) for x in g[:4]], *[_ptr(x) for x in sc[:4]], _ptr(g[4]),
+                    _ptr(sc[4]))
+    k = 5 if m.logpi is not None else 4
+    return (tuple(g[:k]), tuple(sc[:k])) if with_scale else tuple(g[:k])
 
 
 def adam(p, g, m_, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):
@@ -269,15 +282,17 @@ def lr_mu(lr0: float, lr1: float, it: int, n_it: int) -> float:
 
 def fit(m: Model, target, n_it: int, lr=(1e-2, 1e-2, 1e-2, 1e-2, 1e-2),
         b1=0.9, b2=0.999, eps=1e-8):
-    """FP64 Adam fit on the MSE (Sec. VI-B).  lr = (mu0, mu1, chol, ea, eW).
+    """FP64 Adam fit on the MSE (Sec. VI-B).  lr = (mu0, mu1, chol, ea, eW)
+    and, for a model with gate weights, a sixth rate for logpi.
     Updates m's parameters in place; returns the loss history (n_it,)."""
     lib = _load()
     c = m._c()
     t_ = np.ascontiguousarray(target, dtype=np.float32)
-    lr_ = np.ascontiguousarray(lr, dtype=np.float64)
+    lr6 = list(lr) + [0.0] * (6 - len(lr))
+    lr_ = np.ascontiguousarray(lr6[:6], dtype=np.float64)
     loss = np.zeros(n_it, np.float64)
     lib.om_fit(ctypes.byref(c), _ptr(t_), n_it, _ptr(lr_), b1, b2, eps, _ptr(m.mu),
-               _ptr(m.chol), _ptr(m.ea), _ptr(m.eW), _ptr(loss))
+               _ptr(m.chol), _ptr(m.ea), _ptr(m.eW), _ptr(m.logpi), _ptr(loss))
     return loss
 
 

@@ -7,8 +7,11 @@
  * What it computes (paper: "Rasterized Steered Mixture of Experts for
  * Efficient 2D Image Regression", arXiv 2510.05814):
  *   K_k(x) = exp(-1/2 (x-mu_k)^T P_k (x-mu_k)),  P_k = L_k L_k^T       (Eq. 2)
- *   w_k(x) = K_k(x) / sum_i K_i(x)          (Eq. 4 with pi_k = 1)
+ *   w_k(x) = pi_k K_k(x) / sum_i pi_i K_i(x)      (Eq. 4; pi_k = exp(logpi_k),
+ *                                                  pi = 1 when logpi is NULL)
  *   y(x)   = sum_k m_k(x) w_k(x)             (Eq. 3, restricted as in Eq. 5)
+ * or, in the RBF mode (rbf = 1, the Gaussian-splatting regression of Eq. 1),
+ *   y(x)   = sum_k m_k(x) pi_k K_k(x)        (no normalisation: D = 1)
  * with the kernel support truncated (Sec. IV): a pair (pixel, kernel) takes
  * part only if its Mahalanobis distance q is <= q_max.  Every pixel is
  * evaluated against EVERY kernel (no binning): the truncated model is defined
@@ -44,6 +47,8 @@ typedef struct {
     float qmax, scale;
     int64_t K;
     const float *mu, *chol, *ea, *eW;
+    int32_t rbf;            /* 0: softmax gates (Eq. 4); 1: RBF sum (Eq. 1) */
+    const float *logpi;     /* K gate weights log pi_k (Eq. 4), or NULL: pi = 1 */
 } om_model;
 
 /* ------------------------------------------------------------------------ */
@@ -204,7 +209,8 @@ static void pair_value_at(const om_model *m, int64_t k, double x, double y,
     double z1 = (double)c * dy;
     double q = z0 * z0 + z1 * z1;
     pr->dx = dx; pr->dy = dy; pr->z0 = z0; pr->z1 = z1;
-    pr->e = exp(-0.5 * q);                               /* Eq. 2 */
+    double lp = m->logpi ? (double)m->logpi[k] : 0.0;
+    pr->e = exp(lp - 0.5 * q);                     /* pi_k K_k(x), Eqs. 2 and 4 */
     for (int ch = 0; ch < m->C; ++ch) {
         double v = (double)m->ea[k * m->C + ch];
         if (m->linear) {
@@ -270,9 +276,10 @@ void om_render(const om_model *m, int64_t n_px, const int64_t *px, double *y,
         int32_t i = (int32_t)(f % m->W), j = (int32_t)(f / m->W);
         double D, N[3], A[3];
         pixel_sums(m, i, j, &D, N, A);
+        double nrm = m->rbf ? 1.0 : D;      /* Eq. 4 normalises by D, Eq. 1 does not */
         for (int ch = 0; ch < m->C; ++ch) {
-            y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;
-            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / D : 0.0;
+            y[ch * n + p] = D > 0.0 ? N[ch] / nrm : 0.0;
+            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / nrm : 0.0;
         }
         if (invd) invd[p] = D > 0.0 ? 1.0 / D : 0.0;
     }
@@ -295,9 +302,10 @@ void om_render_points(const om_model *m, int64_t n, const float *xy, double *y,
         double D = 0.0, N[3] = {0.0, 0.0, 0.0}, A[3] = {0.0, 0.0, 0.0};
         if (x >= 0.0f && x < (float)m->W && yy >= 0.0f && yy < (float)m->H)
             point_sums(m, x, yy, &D, N, A);
+        double nrm = m->rbf ? 1.0 : D;
         for (int ch = 0; ch < m->C; ++ch) {
-            y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;
-            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / D : 0.0;
+            y[ch * n + p] = D > 0.0 ? N[ch] / nrm : 0.0;
+            if (absm) absm[ch * n + p] = D > 0.0 ? A[ch] / nrm : 0.0;
         }
         if (invd) invd[p] = D > 0.0 ? 1.0 / D : 0.0;
     }
@@ -306,20 +314,23 @@ void om_render_points(const om_model *m, int64_t n, const float *xy, double *y,
 /* Backward pass of the truncated model (the gradient-descent fit of Sec. III-D
  * through the rasteriser), FP64, summed over all pixels.  Upstream gradient:
  * gy (C x H x W) if non-NULL, else the MSE against target,
- * G = 2 (y - t) / (C H W).  For an included pair with gate g = e / D,
- * s = g * sum_c G_c (m_c - y_c):
+ * G = 2 (y - t) / (C H W).  For an included pair with e = pi K, gate
+ * g = e / D and s = g * sum_c G_c (m_c - y_c) (RBF mode: g = e and
+ * s = g * sum_c G_c m_c):
  *   dL/da = -s z0 dx, dL/db = -s z0 dy, dL/dc = -s z1 dy,
  *   dL/dmu_px = (s z0 a, s (z0 b + z1 c)) - g eW^T G   (last term: linear),
- *   dL/dea_c = g G_c,  dL/deW_c = g G_c (dx, dy).
+ *   dL/dea_c = g G_c,  dL/deW_c = g G_c (dx, dy),  dL/dlogpi = s.
  * The indicator [q32 <= q_max] is locally constant (a.e. derivative).  Then
  * the chain rule to API units: dL/dmu_n = dL/dmu_px * (W, H) and
  * dL/d(a,b,c,eW) = dL/d(a',b',c',eW') / s.
  * ksel == NULL: all K kernels, outputs indexed by k.  Otherwise only the n_sel
- * listed kernels, outputs indexed by position in ksel. */
+ * listed kernels, outputs indexed by position in ksel.  g_pi / s_pi (the
+ * gate-weight gradient and its term-magnitude sum) may be NULL. */
 void om_backward(const om_model *m, const double *gy, const float *target,
                  int64_t n_sel, const int64_t *ksel, double *g_mu,
                  double *g_chol, double *g_ea, double *g_eW, double *s_mu,
-                 double *s_chol, double *s_ea, double *s_eW)
+                 double *s_chol, double *s_ea, double *s_eW, double *g_pi,
+                 double *s_pi)
 {
     const int64_t HW = (int64_t)m->W * m->H;
     const int C = m->C;
@@ -346,7 +357,7 @@ void om_backward(const om_model *m, const double *gy, const float *target,
         pixel_sums(m, i, j, &d, N, NULL);
         D[p] = d;
         for (int ch = 0; ch < C; ++ch) {
-            double yv = d > 0.0 ? N[ch] / d : 0.0;
+            double yv = d > 0.0 ? N[ch] / (m->rbf ? 1.0 : d) : 0.0;
             Y[ch * HW + p] = yv;
             G[ch * HW + p] = gy ? gy[ch * HW + p]
                                 : norm * (yv - (double)target[ch * HW + p]);
@@ -357,7 +368,7 @@ void om_backward(const om_model *m, const double *gy, const float *target,
         int64_t k = ksel ? ksel[s] : s;
         float mx, my, a, b, c;
         kernel_px(m, k, &mx, &my, &a, &b, &c);
-        double ga = 0, gb = 0, gc = 0, gmx = 0, gmy = 0;
+        double ga = 0, gb = 0, gc = 0, gmx = 0, gmy = 0, gpi = 0, spi = 0;
         double gea[3] = {0, 0, 0}, gw[3][2] = {{0, 0}, {0, 0}, {0, 0}};
         /* the same sums with every factor replaced by its magnitude: the
          * size of the terms that cancel (optional outputs s_*) */
@@ -376,15 +387,19 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             if (!om_included(m, k, i, j)) continue;
             om_pair pr;
             pair_value(m, k, i, j, &pr);
-            double g = pr.e / D[p];
+            /* softmax: dy/de_k = (m_k - y) / D; RBF: dy/de_k = m_k */
+            double g = m->rbf ? pr.e : pr.e / D[p];
             double r = 0.0;
             for (int ch = 0; ch < C; ++ch)
-                r += G[ch * HW + p] * (pr.mexp[ch] - Y[ch * HW + p]);
+                r += G[ch * HW + p] * (pr.mexp[ch] - (m->rbf ? 0.0 : Y[ch * HW + p]));
             double sv = g * r;
             double sabs = 0.0;
             for (int ch = 0; ch < C; ++ch)
-                sabs += fabs(G[ch * HW + p]) * (fabs(pr.mexp[ch]) + fabs(Y[ch * HW + p]));
+                sabs += fabs(G[ch * HW + p]) *
+                        (fabs(pr.mexp[ch]) + (m->rbf ? 0.0 : fabs(Y[ch * HW + p])));
             sabs *= g;
+            gpi += sv;                                /* d e_k / d logpi_k = e_k */
+            spi += sabs;
             sa += sabs * fabs(pr.z0 * pr.dx);
             sb += sabs * fabs(pr.z0 * pr.dy);
             sc += sabs * fabs(pr.z1 * pr.dy);
@@ -412,6 +427,8 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             }
         }
         double inv_s = 1.0 / (double)m->scale;
+        if (g_pi) g_pi[s] = gpi;
+        if (s_pi) s_pi[s] = spi;
         g_mu[2 * s] = gmx * (double)m->W;
         g_mu[2 * s + 1] = gmy * (double)m->H;
         g_chol[3 * s] = ga * inv_s;
@@ -469,18 +486,20 @@ double om_lr_mu(double lr0, double lr1, int32_t it, int32_t n_it)
  * loss.  Master parameters and Adam state are FP64; each iteration evaluates
  * the model at the float rounding of the master parameters.  lr = {mu0, mu1,
  * chol, ea, eW}.  loss[it] receives the MSE (unclamped, before the update of
- * iteration it).  Parameters are updated in place (float outputs). */
-void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[5],
+ * iteration it).  Parameters are updated in place (float outputs).  With
+ * logpi non-NULL the gate weights are a fifth group at rate lr[5]. */
+void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[6],
             double b1, double b2, double eps, float *mu, float *chol,
-            float *ea, float *eW, double *loss)
+            float *ea, float *eW, float *logpi, double *loss)
 {
     const int64_t K = m->K;
     const int C = m->C;
     const int64_t HW = (int64_t)m->W * m->H;
-    int64_t n_g[4] = {2 * K, 3 * K, (int64_t)C * K, m->linear ? 2 * (int64_t)C * K : 0};
-    float *fp[4] = {mu, chol, ea, eW};
-    double *P[4], *G[4], *M[4], *V[4];
-    for (int gi = 0; gi < 4; ++gi) {
+    int64_t n_g[5] = {2 * K, 3 * K, (int64_t)C * K, m->linear ? 2 * (int64_t)C * K : 0,
+                      logpi ? K : 0};
+    float *fp[5] = {mu, chol, ea, eW, logpi};
+    double *P[5], *G[5], *M[5], *V[5];
+    for (int gi = 0; gi < 5; ++gi) {
         size_t n = (size_t)(n_g[gi] > 0 ? n_g[gi] : 1);
         P[gi] = (double *)calloc(n, sizeof(double));
         G[gi] = (double *)calloc(n, sizeof(double));
@@ -489,9 +508,9 @@ void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[5],
         for (int64_t x = 0; x < n_g[gi]; ++x) P[gi][x] = (double)fp[gi][x];
     }
     double *y = (double *)malloc(sizeof(double) * (size_t)(HW * C));
-    m->mu = mu; m->chol = chol; m->ea = ea; m->eW = eW;
+    m->mu = mu; m->chol = chol; m->ea = ea; m->eW = eW; m->logpi = logpi;
     for (int32_t it = 0; it < n_it; ++it) {
-        for (int gi = 0; gi < 4; ++gi)
+        for (int gi = 0; gi < 5; ++gi)
             for (int64_t x = 0; x < n_g[gi]; ++x) fp[gi][x] = (float)P[gi][x];
         if (loss) {
             om_render(m, 0, NULL, y, NULL, NULL);
@@ -503,14 +522,15 @@ void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[5],
             loss[it] = se / (double)(HW * C);
         }
         om_backward(m, NULL, target, 0, NULL, G[0], G[1], G[2],
-                    m->linear ? G[3] : NULL, NULL, NULL, NULL, NULL);
-        double lrs[4] = {om_lr_mu(lr[0], lr[1], it, n_it), lr[2], lr[3], lr[4]};
-        for (int gi = 0; gi < 4; ++gi)
+                    m->linear ? G[3] : NULL, NULL, NULL, NULL, NULL,
+                    logpi ? G[4] : NULL, NULL);
+        double lrs[5] = {om_lr_mu(lr[0], lr[1], it, n_it), lr[2], lr[3], lr[4], lr[5]};
+        for (int gi = 0; gi < 5; ++gi)
             if (n_g[gi] > 0)
                 om_adam(n_g[gi], P[gi], G[gi], M[gi], V[gi], lrs[gi], b1, b2,
                         eps, it + 1);
     }
-    for (int gi = 0; gi < 4; ++gi) {
+    for (int gi = 0; gi < 5; ++gi) {
         for (int64_t x = 0; x < n_g[gi]; ++x) fp[gi][x] = (float)P[gi][x];
         free(P[gi]); free(G[gi]); free(M[gi]); free(V[gi]);
     }

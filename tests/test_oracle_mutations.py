@@ -17,7 +17,13 @@ MUTATIONS = {
     "transposed_L": ("float z0 = fmaf(a, dx, t);", "float z0 = fmaf(a, dx, 0.0f);"),
     "wrong_cross_term": ("double z0 = (double)a * dx + (double)b * dy;",
                          "double z0 = (double)a * dx - (double)b * dy;"),
-    "missing_half": ("pr->e = exp(-0.5 * q);", "pr->e = exp(-q);"),
+    "missing_half": ("pr->e = exp(lp - 0.5 * q);", "pr->e = exp(lp - q);"),
+    "gate_weight_ignored": ("double lp = m->logpi ? (double)m->logpi[k] : 0.0;",
+                            "double lp = 0.0;"),
+    "gate_weight_grad_sign": ("gpi += sv;", "gpi -= sv;"),
+    "rbf_normalised": ("double nrm = m->rbf ? 1.0 : D;", "double nrm = D;"),
+    "rbf_grad_keeps_y": ("r += G[ch * HW + p] * (pr.mexp[ch] - (m->rbf ? 0.0 : Y[ch * HW + p]));",
+                         "r += G[ch * HW + p] * (pr.mexp[ch] - Y[ch * HW + p]);"),
     "swapped_slope_index": ("v += w0 * dx + w1 * dy;", "v += w1 * dx + w0 * dy;"),
     "dropped_expert_mu_term": ("gmx -= gG * w[ch][0];", "gmx -= 0.0;"),
     "sign_grad_c": ("gc += -sv * pr.z1 * pr.dy;", "gc += sv * pr.z1 * pr.dy;"),
@@ -25,8 +31,8 @@ MUTATIONS = {
     "box_uses_min_axis": ("float lmax_p = half_tr + rt;", "float lmax_p = half_tr - rt;"),
     "adam_no_bias_correction": ("double bc1 = 1.0 - pow(b1, (double)step);", "double bc1 = 1.0;"),
     "predicate_strict": ("return q32 <= m->qmax;", "return q32 < m->qmax - 1e-3f;"),
-    "empty_rule": ("y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.0;",
-                   "y[ch * n + p] = D > 0.0 ? N[ch] / D : 0.5;"),
+    "empty_rule": ("y[ch * n + p] = D > 0.0 ? N[ch] / nrm : 0.0;",
+                   "y[ch * n + p] = D > 0.0 ? N[ch] / nrm : 0.5;"),
     "points_swapped_xy": ("float x = xy[2 * p], yy = xy[2 * p + 1];",
                           "float x = xy[2 * p + 1], yy = xy[2 * p];"),
     "points_no_raster_bounds": ("if (x >= 0.0f && x < (float)m->W && yy >= 0.0f && yy < (float)m->H)",

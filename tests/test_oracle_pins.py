@@ -330,13 +330,17 @@ def test_super_resolution_linear_expert(om):
 
 # ---------------------------------------------------------------- backward
 
-def dense_torch_loss(m, mask, gy, scale=1.0):
-    """The truncated model written densely in torch float64 (for autograd)."""
+def dense_torch_loss(m, mask, gy, scale=1.0, with_y=False):
+    """The truncated model written densely in torch float64 (for autograd):
+    softmax gates with weights pi = exp(logpi) (Eq. 4), or the RBF sum of
+    Eq. 1 when m.rbf."""
     import torch
     mu = torch.tensor(m.mu, dtype=torch.float64, requires_grad=True)
     chol = torch.tensor(m.chol, dtype=torch.float64, requires_grad=True)
     ea = torch.tensor(m.ea, dtype=torch.float64, requires_grad=True)
     eW = torch.tensor(m.eW, dtype=torch.float64, requires_grad=True) if m.linear else None
+    lp = (torch.tensor(m.logpi, dtype=torch.float64, requires_grad=True)
+          if m.logpi is not None else None)
     jj, ii = torch.meshgrid(torch.arange(m.H, dtype=torch.float64),
                             torch.arange(m.W, dtype=torch.float64), indexing="ij")
     X = torch.stack([ii.reshape(-1) + 0.5, jj.reshape(-1) + 0.5], 1)          # (HW, 2)
@@ -356,15 +360,24 @@ def dense_torch_loss(m, mask, gy, scale=1.0):
     d = X[:, None, :] - centre[None]                                             # (HW, K, 2)
     z0 = Lf[:, 0] * d[..., 0] + Lf[:, 1] * d[..., 1]
     z1 = Lf[:, 2] * d[..., 1]
-    e = torch.exp(-0.5 * (z0 * z0 + z1 * z1)) * torch.tensor(mask, dtype=torch.float64)
+    arg = -0.5 * (z0 * z0 + z1 * z1)
+    if lp is not None:
+        arg = arg + lp[None]
+    e = torch.exp(arg) * torch.tensor(mask, dtype=torch.float64)
     mexp = ea[None].expand(X.shape[0], -1, -1)
     if m.linear:
         mexp = mexp + torch.einsum("kcd,pkd->pkc", fdiv(eW), d)
     D = e.sum(1)
-    y = (e[..., None] * mexp).sum(1) / torch.where(D > 0, D, torch.ones_like(D))[:, None]
+    if m.rbf:
+        y = (e[..., None] * mexp).sum(1)
+    else:
+        y = (e[..., None] * mexp).sum(1) / torch.where(D > 0, D, torch.ones_like(D))[:, None]
     loss = (y.T.reshape(m.C, m.H, m.W) * torch.tensor(gy)).sum()
-    grads = torch.autograd.grad(loss, [mu, chol, ea] + ([eW] if m.linear else []))
-    return [g.numpy() for g in grads]
+    leaves = [mu, chol, ea] + ([eW] if m.linear else []) + ([lp] if lp is not None else [])
+    grads = [g.numpy() for g in torch.autograd.grad(loss, leaves)]
+    if with_y:
+        return grads, y.detach().T.reshape(m.C, m.H, m.W).numpy()
+    return grads
 
 
 def inclusion_mask(om, m):
@@ -372,19 +385,31 @@ def inclusion_mask(om, m):
                      for p in range(m.W * m.H)], np.float64)
 
 
-@pytest.mark.parametrize("linear,scale", [(False, 1.0), (True, 1.0), (True, 1.5)])
-def test_backward_matches_torch_autograd(om, linear, scale):
+@pytest.mark.parametrize("linear,scale,pi,rbf", [(False, 1.0, False, False),
+                                                  (True, 1.0, False, False),
+                                                  (True, 1.5, False, False),
+                                                  (True, 1.0, True, False),
+                                                  (False, 1.0, True, True),
+                                                  (True, 1.5, True, True)])
+def test_backward_matches_torch_autograd(om, linear, scale, pi, rbf):
     """Analytic backward (the a.e. gradient of the truncated model) equals
-    torch float64 autograd of the dense formula, for all four groups."""
+    torch float64 autograd of the dense formula, for every parameter group:
+    softmax gates with and without gate weights pi (Eq. 4), and the RBF sum
+    of Eq. 1; the renders agree as well."""
     rng = np.random.default_rng(7)
     m = rand_model(om, rng, W=22, H=18, K=9, linear=linear, sig=(2.0, 5.0))
     m.W, m.H, m.scale = int(22 * scale), int(18 * scale), scale
+    if pi:
+        m.logpi = rng.normal(0, 0.7, m.K).astype(np.float32)
+    m.rbf = rbf
     gy = rng.normal(0, 1, (m.C, m.H, m.W))
     mask = inclusion_mask(om, m)
-    ref = dense_torch_loss(m, mask, gy, scale)
-    got = om.backward(m, gy=gy)
+    ref, y_ref = dense_torch_loss(m, mask, gy, scale, with_y=True)
+    got = [g for g in om.backward(m, gy=gy) if g is not None]
+    assert len(got) == len(ref)
     for r, g in zip(ref, got):
         np.testing.assert_allclose(g, r, rtol=1e-9, atol=1e-12 * np.abs(r).max())
+    np.testing.assert_allclose(om.render(m)[0], y_ref, rtol=1e-12, atol=1e-14)
 
 
 def test_backward_fused_mse_and_selected_kernels(om):
@@ -728,3 +753,102 @@ def test_sharpen_large_factor_tends_to_hard_assignment(om):
             assert abs(y[0, j, i] - mmin) <= bound * (1 + 1e-6) + 1e-6
             n_hard += bound < 1e-3
     assert n_hard > 100
+
+
+# ---------------------------------------------------------------- gate weights and the RBF mode
+
+def test_gate_weights_two_kernel_logistic(om):
+    """Eq. 4 with weights: two constant experts give
+    y = m2 + (m1 - m2) expit((q2 - q1)/2 + logpi1 - logpi2)."""
+    m = om.Model(32, 16, 1, np.array([[0.35, 0.5], [0.6, 0.45]]),
+                 np.array([[0.2, 0.05, 0.18], [0.15, -0.04, 0.22]]), np.array([[0.1], [0.9]]),
+                 logpi=np.array([0.8, -0.35]))
+    y, _ = om.render(m)
+    l1, l2 = float(np.float32(0.8)), float(np.float32(-0.35))
+    m1, m2 = float(np.float32(0.1)), float(np.float32(0.9))
+    n = 0
+    for j in range(m.H):
+        for i in range(m.W):
+            if om.included(m, 0, i, j) and om.included(m, 1, i, j):
+                n += 1
+                q1, q2 = q64(m, 0, i, j), q64(m, 1, i, j)
+                ref = m2 + (m1 - m2) * scipy.special.expit(0.5 * (q2 - q1) + l1 - l2)
+                assert y[0, j, i] == pytest.approx(ref, rel=1e-12)
+    assert n > 50
+
+
+def test_gate_weights_shift_invariance(om):
+    """The softmax is invariant to a common factor on every pi: adding c to
+    every logpi leaves y unchanged, and so the gate-weight gradients sum to
+    zero at every pixel and over the image (d/dc of the loss is 0)."""
+    rng = np.random.default_rng(80)
+    m = rand_model(om, rng, W=24, H=20, K=12, linear=True)
+    # multiples of 2^-10, so that adding 1.25 is exact in float32
+    m.logpi = (rng.integers(-600, 600, m.K) / 1024.0).astype(np.float32)
+    y0, _ = om.render(m)
+    m2 = om.Model(m.W, m.H, m.C, m.mu, m.chol, m.ea, m.eW, tile=m.tile, logpi=m.logpi + 1.25)
+    np.testing.assert_allclose(om.render(m2)[0], y0, rtol=1e-12, atol=1e-14)
+    gy = rng.normal(0, 1, (m.C, m.H, m.W))
+    g, sc = om.backward(m, gy=gy, with_scale=True)
+    assert abs(g[4].sum()) <= 1e-12 * sc[4].sum()
+    assert np.abs(g[4]).max() > 1e-3
+
+
+def test_gate_weight_central_differences(om):
+    rng = np.random.default_rng(81)
+    for rbf in (False, True):
+        m = rand_model(om, rng, W=18, H=16, K=6, sig=(2.5, 4.0))
+        m.logpi = rng.normal(0, 0.5, m.K).astype(np.float32)
+        m.rbf = rbf
+        gy = rng.normal(0, 1, (m.C, m.H, m.W))
+        g = om.backward(m, gy=gy)[4]
+        for k in range(m.K):
+            v0 = m.logpi[k]
+            h = np.float32(1e-3)
+            vals = []
+            for sgn in (1, -1):
+                m.logpi[k] = np.float32(v0 + sgn * h)
+                vals.append(float((om.render(m)[0] * gy).sum()))
+            m.logpi[k] = v0
+            real_h = (float(np.float32(v0 + h)) - float(np.float32(v0 - h))) / 2
+            fd = (vals[0] - vals[1]) / (2 * real_h)
+            assert fd == pytest.approx(g[k], rel=1e-5, abs=1e-7 * np.abs(g).max()), (rbf, k)
+
+
+def test_rbf_single_kernel_and_superposition(om):
+    """Eq. 1: with no normalisation a single kernel renders pi K(x) m(x)
+    (not m(x)), and the render of a model is the sum of the renders of its
+    kernels taken one at a time (superposition), unlike the softmax gates."""
+    rng = np.random.default_rng(82)
+    m = rand_model(om, rng, W=22, H=18, K=5, linear=True, sig=(2.0, 4.0))
+    m.logpi = rng.normal(0, 0.5, m.K).astype(np.float32)
+    m.rbf = True
+    y, _ = om.render(m)
+    parts = np.zeros_like(y)
+    for k in range(m.K):
+        one = om.Model(m.W, m.H, m.C, m.mu[k:k + 1], m.chol[k:k + 1], m.ea[k:k + 1],
+                       m.eW[k:k + 1], tile=m.tile, logpi=m.logpi[k:k + 1], rbf=True)
+        yk, _ = om.render(one)
+        c, _ = kernel_px64(m, k)
+        for j in range(m.H):
+            for i in range(m.W):
+                if om.included(m, k, i, j):
+                    q = q64(m, k, i, j)
+                    mexp = m.ea[k] + m.eW[k].astype(np.float64) @ (np.array([i + 0.5, j + 0.5]) - c)
+                    ref = math.exp(float(m.logpi[k]) - 0.5 * q) * mexp
+                    np.testing.assert_allclose(yk[:, j, i], ref, rtol=1e-12, atol=1e-15)
+                else:
+                    assert np.all(yk[:, j, i] == 0)
+        parts += yk
+    np.testing.assert_allclose(y, parts, rtol=1e-12, atol=1e-15)
+    m.rbf = False
+    assert np.abs(om.render(m)[0] - parts).max() > 1e-2
+
+
+def test_fit_with_gate_weights_decreases_loss(om):
+    t = synth.polygon_image(24, 20, 3, 3, 83)
+    p = synth.init_params(t, 16, 3.0, True, 83)
+    m = om.Model(24, 20, 3, p.mu, p.chol, p.ea, p.eW, tile=8, logpi=np.zeros(16, np.float32))
+    loss = om.fit(m, t, 15, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2, 5e-2))
+    assert loss[-1] < 0.9 * loss[0]
+    assert np.abs(m.logpi).max() > 1e-3            # the weights moved
