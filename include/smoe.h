@@ -82,6 +82,8 @@ typedef struct {
                          at most 174, so that exp(-q/2) of every included pair is a
                          normal FP32 number (larger values: SMOE_ERR_ARG) */
     float scale;      /* resampling scale s >= 0: L' = L / s, eW' = eW / s; 1 for a fit */
+    int32_t gate;     /* 0 = SMoE softmax gates (Eq. 4): y = N / D;
+                         1 = RBF / Gaussian-splatting regression (Eq. 1): y = N, D = 1 */
 } smoe_desc;
 
 /* Parameters (or gradients, or Adam moments) of K kernels, all device SoA. */
@@ -91,6 +93,8 @@ typedef struct {
     float *chol;      /* K x 3 */
     float *ea;        /* K x C */
     float *eW;        /* K x C x 2, NULL for constant experts */
+    float *logpi;     /* K gate weights log pi_k (Eq. 4: pi_k = exp(logpi_k)), or NULL
+                         for pi = 1.  Gradients and moments carry it when p does. */
 } smoe_params;
 
 /* Library version, (major << 16) | minor. */
@@ -120,8 +124,8 @@ SMOE_API smoe_status smoe_bin(const smoe_desc *d, const smoe_params *p, void *ws
                      int64_t *n_pairs, int32_t *status, void *stream);
 
 /* Forward render per tile (Eqs. 2-5): y_c = N_c / D with N_c = sum e m_c,
- * D = sum e over the tile's list, e = exp(-q/2) [q32 <= q_max].  FP32
- * accumulation.  Reads the prepared records that smoe_bin left in `ws` (same
+ * D = sum e over the tile's list, e = pi exp(-q/2) [q32 <= q_max] (d->gate = 1:
+ * y_c = N_c, Eq. 1).  FP32 accumulation.  Reads the prepared records that smoe_bin left in `ws` (same
  * desc and parameters).
  *   y      out: C x H x W (device)
  *   inv_d  out: H x W, 1/D (0 where D = 0), or NULL (device)
@@ -145,12 +149,13 @@ SMOE_API smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params 
                                  void *stream);
 
 /* Adam (Sec. VI-B), torch semantics, FP32 state, one fused launch over the
- * four parameter groups; zeroes g.  1 - b1, 1 - b2 and the bias corrections
- * are formed in FP64 and rounded once.  lr = {mu, chol, ea, eW}; step >= 1 is the
- * 1-based step used for the bias corrections.  C is the channel count
- * (sizes of ea / eW).  eW pointers must all be NULL or all non-NULL. */
+ * parameter groups; zeroes g.  1 - b1, 1 - b2 and the bias corrections
+ * are formed in FP64 and rounded once.  lr = {mu, chol, ea, eW, logpi}; step >= 1
+ * is the 1-based step used for the bias corrections.  C is the channel count
+ * (sizes of ea / eW).  eW pointers must all be NULL or all non-NULL, and so must
+ * the logpi pointers. */
 SMOE_API smoe_status smoe_adam_step(const smoe_params *p, const smoe_params *g, const smoe_params *m,
-                           const smoe_params *v, int32_t C, const float lr[4], double b1,
+                           const smoe_params *v, int32_t C, const float lr[5], double b1,
                            double b2, double eps, int32_t step, void *stream);
 
 /* Sum of squared differences over n floats, FP64 accumulation, ADDED to
@@ -172,6 +177,7 @@ typedef struct {
     int32_t iters;          /* length of this image's run (lr schedule, loss history) */
     float lr_mu0, lr_mu1;   /* centre rate, decayed exponentially lr_mu0 -> lr_mu1 */
     float lr_chol, lr_ea, lr_eW;
+    float lr_pi;            /* rate of the gate weights (used when p.logpi is set) */
 } smoe_fit_image;
 
 typedef struct {
@@ -189,6 +195,7 @@ typedef struct {
                                tile order, so a fit is bit-reproducible and independent of
                                the other images in the batch (costs 64 B per pair of
                                workspace); 0: float atomics (faster, order-dependent) */
+    int32_t gate;           /* as smoe_desc.gate: 0 softmax gates, 1 RBF sum */
 } smoe_fit_batch;
 
 /* Workspace bytes for a fit of this batch with pair_cap pairs in total. */

@@ -174,7 +174,9 @@ def bin_tiles(m: Model, tiles=None):
 def render(m: Model, pixels=None, with_scale=False):
     """FP64 render.  Returns (y, invd): y is (C,H,W) for a full render or
     (C,n) for the listed flat pixel indices; invd likewise (H,W) or (n,).
-    with_scale=True also returns sum_k w_k |m_k| in y's layout."""
+    with_scale=True also returns, in y's layout, sum_k w_k times the sum of the
+    magnitudes of the terms of m_k (|a| + |W0 dx| + |W1 dy|): the scale of
+    the rounding error of the gated sum."""
     lib = _load()
     c = m._c()
     sel = None if pixels is None else np.ascontiguousarray(pixels, dtype=np.int64)

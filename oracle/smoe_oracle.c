@@ -196,7 +196,7 @@ int64_t om_bin(const om_model *m, int64_t n_sel, const int64_t *tiles,
 /* Gate numerator and expert of kernel k at pixel (i, j), FP64, for an
  * included pair.  dx, dy use the FP32 kernel centre (the model's centre is
  * defined as the float product mu_n * W); the rest is exact FP64. */
-typedef struct { double dx, dy, z0, z1, e; double mexp[3]; } om_pair;
+typedef struct { double dx, dy, z0, z1, e; double mexp[3], mabs[3]; } om_pair;
 
 static void pair_value_at(const om_model *m, int64_t k, double x, double y,
                           om_pair *pr)
@@ -222,6 +222,9 @@ static void pair_value_at(const om_model *m, int64_t k, double x, double y,
                 w1 = (double)(m->eW[(k * m->C + ch) * 2 + 1] / m->scale);
             }
             v += w0 * dx + w1 * dy;
+            pr->mabs[ch] = fabs((double)m->ea[k * m->C + ch]) + fabs(w0 * dx) + fabs(w1 * dy);
+        } else {
+            pr->mabs[ch] = fabs(v);
         }
         pr->mexp[ch] = v;
     }
@@ -235,7 +238,8 @@ static void pair_value(const om_model *m, int64_t k, int32_t i, int32_t j,
 
 /* Gate denominator D and numerators N_c at the sample point (x, y) (FP32
  * pixel units) over all K kernels; A_c (if non-NULL) receives
- * sum_k e_k |m_kc|, the scale of the sum. */
+ * sum_k e_k (|a_kc| + |W_kc0 dx| + |W_kc1 dy|), the size of the terms that
+ * make up the gated sum (the scale of its rounding error). */
 static void point_sums(const om_model *m, float x, float y, double *D,
                        double *N, double *A)
 {
@@ -248,7 +252,7 @@ static void point_sums(const om_model *m, float x, float y, double *D,
         d += pr.e;
         for (int ch = 0; ch < m->C; ++ch) {
             N[ch] += pr.e * pr.mexp[ch];
-            if (A) A[ch] += pr.e * fabs(pr.mexp[ch]);
+            if (A) A[ch] += pr.e * pr.mabs[ch];
         }
     }
     *D = d;
@@ -264,8 +268,9 @@ static void pixel_sums(const om_model *m, int32_t i, int32_t j, double *D,
  * included kernel (D = 0) gets y = 0 and invd = 0.  px == NULL renders all
  * H*W pixels in row-major order; otherwise the n_px listed flat pixel indices
  * (j*W + i).  y is channel-planar over the rendered pixels: y[c*n + p].
- * absm (optional, same layout as y) receives sum_k w_k |m_kc|, the size of
- * the terms of the gated sum (used to scale a tolerance). */
+ * absm (optional, same layout as y) receives sum_k w_k (|a_kc| + |W_kc (x - mu_k)|
+ * taken term by term), the size of the terms of the gated sum (used to scale
+ * a tolerance). */
 void om_render(const om_model *m, int64_t n_px, const int64_t *px, double *y,
                double *invd, double *absm)
 {
@@ -396,7 +401,7 @@ void om_backward(const om_model *m, const double *gy, const float *target,
             double sabs = 0.0;
             for (int ch = 0; ch < C; ++ch)
                 sabs += fabs(G[ch * HW + p]) *
-                        (fabs(pr.mexp[ch]) + (m->rbf ? 0.0 : fabs(Y[ch * HW + p])));
+                        (pr.mabs[ch] + (m->rbf ? 0.0 : fabs(Y[ch * HW + p])));
             sabs *= g;
             gpi += sv;                                /* d e_k / d logpi_k = e_k */
             spi += sabs;

@@ -27,12 +27,12 @@ class SmoeError(RuntimeError):
 class Desc(ctypes.Structure):
     _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("C", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("expert", ctypes.c_int32),
-                ("qmax", ctypes.c_float), ("scale", ctypes.c_float)]
+                ("qmax", ctypes.c_float), ("scale", ctypes.c_float), ("gate", ctypes.c_int32)]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int64), ("mu", ctypes.c_void_p), ("chol", ctypes.c_void_p),
-                ("ea", ctypes.c_void_p), ("eW", ctypes.c_void_p)]
+                ("ea", ctypes.c_void_p), ("eW", ctypes.c_void_p), ("logpi", ctypes.c_void_p)]
 
 
 class FitImage(ctypes.Structure):
@@ -40,7 +40,7 @@ class FitImage(ctypes.Structure):
                 ("p", Params), ("m", Params), ("v", Params),
                 ("iters", ctypes.c_int32), ("lr_mu0", ctypes.c_float),
                 ("lr_mu1", ctypes.c_float), ("lr_chol", ctypes.c_float),
-                ("lr_ea", ctypes.c_float), ("lr_eW", ctypes.c_float)]
+                ("lr_ea", ctypes.c_float), ("lr_eW", ctypes.c_float), ("lr_pi", ctypes.c_float)]
 
 
 class FitBatch(ctypes.Structure):
@@ -48,7 +48,8 @@ class FitBatch(ctypes.Structure):
                 ("expert", ctypes.c_int32), ("qmax", ctypes.c_float), ("b1", ctypes.c_double),
                 ("b2", ctypes.c_double), ("eps", ctypes.c_double), ("step", ctypes.c_void_p),
                 ("loss", ctypes.c_void_p), ("hist", ctypes.c_int32),
-                ("persistent", ctypes.c_int32), ("deterministic", ctypes.c_int32)]
+                ("persistent", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("gate", ctypes.c_int32)]
 
 
 _lib = None

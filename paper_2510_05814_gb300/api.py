@@ -30,8 +30,9 @@ def _stream(stream):
 
 @dataclass(frozen=True)
 class RasterDesc:
-    """A raster: W x H pixels, C channels, tile side, expert type, cutoff and
-    resampling scale (L' = L/s, eW' = eW/s)."""
+    """A raster: W x H pixels, C channels, tile side, expert type, cutoff,
+    resampling scale (L' = L/s, eW' = eW/s) and gate mode (rbf: the
+    unnormalised sum of Eq. 1 instead of the softmax gates of Eq. 4)."""
     W: int
     H: int
     C: int
@@ -39,9 +40,11 @@ class RasterDesc:
     linear: bool = True
     qmax: float = 9.0
     scale: float = 1.0
+    rbf: bool = False
 
     def c(self):
-        return _lib.Desc(self.W, self.H, self.C, self.tile, int(self.linear), self.qmax, self.scale)
+        return _lib.Desc(self.W, self.H, self.C, self.tile, int(self.linear), self.qmax, self.scale,
+                         int(self.rbf))
 
     @property
     def n_tiles(self):
@@ -50,30 +53,37 @@ class RasterDesc:
 
 class SMoEParams:
     """Kernel parameters as FP32 CUDA tensors (SoA): mu (K,2) normalised,
-    chol (K,3) = (a,b,c), ea (K,C), eW (K,C,2) or None."""
+    chol (K,3) = (a,b,c), ea (K,C), eW (K,C,2) or None, logpi (K,) gate
+    weights log pi_k (Eq. 4) or None for pi = 1."""
 
-    def __init__(self, mu, chol, ea, eW=None):
-        self.mu, self.chol, self.ea, self.eW = mu, chol, ea, eW
+    def __init__(self, mu, chol, ea, eW=None, logpi=None):
+        self.mu, self.chol, self.ea, self.eW, self.logpi = mu, chol, ea, eW, logpi
 
     @classmethod
     def from_numpy(cls, p, device="cuda"):
         f = lambda a: None if a is None else torch.as_tensor(np.ascontiguousarray(a, np.float32),
                                                               device=device)
-        return cls(f(p.mu), f(p.chol), f(p.ea), f(p.eW))
+        return cls(f(p.mu), f(p.chol), f(p.ea), f(p.eW), f(getattr(p, "logpi", None)))
 
     @classmethod
-    def zeros(cls, K, C, linear, device="cuda"):
+    def zeros(cls, K, C, linear, device="cuda", pi=False):
         z = lambda *s: torch.zeros(*s, dtype=torch.float32, device=device)
-        return cls(z(K, 2), z(K, 3), z(K, C), z(K, C, 2) if linear else None)
+        return cls(z(K, 2), z(K, 3), z(K, C), z(K, C, 2) if linear else None,
+                   z(K) if pi else None)
 
     def zeros_like(self):
-        return SMoEParams(*(None if t is None else torch.zeros_like(t) for t in self.tensors()))
+        return SMoEParams(*(None if t is None else torch.zeros_like(t) for t in self.slots()))
 
     def clone(self):
-        return SMoEParams(*(None if t is None else t.clone() for t in self.tensors()))
+        return SMoEParams(*(None if t is None else t.clone() for t in self.slots()))
+
+    def slots(self):
+        """(mu, chol, ea, eW, logpi), None for an absent group."""
+        return (self.mu, self.chol, self.ea, self.eW, self.logpi)
 
     def tensors(self):
-        return (self.mu, self.chol, self.ea, self.eW)
+        """The groups present, in slot order."""
+        return tuple(t for t in self.slots() if t is not None)
 
     @property
     def K(self):
@@ -88,10 +98,12 @@ class SMoEParams:
         return self.eW is not None
 
     def c(self):
-        return _lib.Params(self.K, _ptr(self.mu), _ptr(self.chol), _ptr(self.ea), _ptr(self.eW))
+        return _lib.Params(self.K, _ptr(self.mu), _ptr(self.chol), _ptr(self.ea), _ptr(self.eW),
+                           _ptr(self.logpi))
 
     def numpy(self):
-        return tuple(None if t is None else t.detach().cpu().numpy() for t in self.tensors())
+        """Host copies of the present groups, in slot order."""
+        return tuple(t.detach().cpu().numpy() for t in self.tensors())
 
 
 # ---------------------------------------------------------------------------
@@ -133,7 +145,9 @@ def smoe_render_backward(desc, params, ws, tile_off, pair_k, y, inv_d, gy, targe
 
 
 def smoe_adam_step(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1, stream=None):
-    lr4 = (ctypes.c_float * 4)(*[float(x) for x in lr])
+    """lr = (mu, chol, ea, eW[, logpi])."""
+    lr5 = list(lr) + [0.0] * (5 - len(lr))
+    lr4 = (ctypes.c_float * 5)(*[float(x) for x in lr5[:5]])
     pc, gc, mc, vc = p.c(), g.c(), m.c(), v.c()
     check(_lib.load().smoe_adam_step(ctypes.byref(pc), ctypes.byref(gc), ctypes.byref(mc),
                                      ctypes.byref(vc), p.C, lr4, float(b1), float(b2),
@@ -257,51 +271,53 @@ def sharpen(params: SMoEParams, factor: float, qmax: float = 9.0):
     return SMoEParams(params.mu, chol, params.ea, params.eW), qmax2
 
 
-def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0, sharpen_factor=None):
+def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0, sharpen_factor=None,
+           rbf=False):
     """Bin and render ``params`` on a W x H raster (``scale`` times the fitted
-    raster, optionally sharpened); returns (y, inv_d, rasterizer)."""
+    raster, optionally sharpened; rbf: the sum of Eq. 1); returns
+    (y, inv_d, rasterizer)."""
     if sharpen_factor is not None and sharpen_factor != 1.0:
         params, qmax = sharpen(params, sharpen_factor, qmax)
-    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, scale)
+    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, scale, rbf)
     r = Rasterizer(desc, params.K).bin(params)
     y, inv_d = r.render()
     return y, inv_d, r
 
 
-def render_points(params: SMoEParams, W, H, xy, tile=16, qmax=9.0, sharpen_factor=None):
+def render_points(params: SMoEParams, W, H, xy, tile=16, qmax=9.0, sharpen_factor=None,
+                  rbf=False):
     """Resample the model fitted on a W x H raster at the (n, 2) points
     ``xy`` (pixel units of that raster): super-resolution on an irregular
     raster.  Returns (y (C, n), inv_d (n,), rasterizer)."""
     if sharpen_factor is not None and sharpen_factor != 1.0:
         params, qmax = sharpen(params, sharpen_factor, qmax)
-    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, 1.0)
+    desc = RasterDesc(W, H, params.C, tile, params.linear, qmax, 1.0, rbf)
     r = Rasterizer(desc, params.K).bin(params)
     y, inv_d = r.render_points(xy)
     return y, inv_d, r
 
 
 class SMoERender(torch.autograd.Function):
-    """y = R-SMoE render of (mu, chol, ea, eW) on a raster (Eqs. 2-5), with the
-    backward of the tile kernels.  Each forward keeps its own lists for its
-    backward."""
+    """y = R-SMoE render of (mu, chol, ea, eW[, logpi]) on a raster (Eqs. 2-5;
+    the RBF sum of Eq. 1 when desc.rbf), with the backward of the tile
+    kernels.  Each forward keeps its own lists for its backward."""
 
     @staticmethod
-    def forward(ctx, mu, chol, ea, eW, desc: RasterDesc):
-        p = SMoEParams(mu.detach().contiguous(), chol.detach().contiguous(),
-                       ea.detach().contiguous(), None if eW is None else eW.detach().contiguous())
+    def forward(ctx, mu, chol, ea, eW, desc: RasterDesc, logpi=None):
+        c = lambda t: None if t is None else t.detach().contiguous()
+        p = SMoEParams(c(mu), c(chol), c(ea), c(eW), c(logpi))
         r = Rasterizer(desc, p.K).bin(p)
         y, inv_d = r.render()
         ctx.r, ctx.p = r, p
         ctx.save_for_backward(y, inv_d)
-        ctx.has_w = eW is not None
         return y
 
     @staticmethod
     def backward(ctx, gy):
         y, inv_d = ctx.saved_tensors
         g = ctx.r.backward(ctx.p, y, inv_d, gy=gy.contiguous())
-        return g.mu, g.chol, g.ea, (g.eW if ctx.has_w else None), None
+        return g.mu, g.chol, g.ea, g.eW, None, g.logpi
 
 
-def smoe_render_fn(mu, chol, ea, eW, desc: RasterDesc):
-    return SMoERender.apply(mu, chol, ea, eW, desc)
+def smoe_render_fn(mu, chol, ea, eW, desc: RasterDesc, logpi=None):
+    return SMoERender.apply(mu, chol, ea, eW, desc, logpi)

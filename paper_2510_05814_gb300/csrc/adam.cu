@@ -27,13 +27,14 @@ __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, con
     p -= k.step_size * (m / denom);
 }
 
-// One launch over the four groups of a SoA parameter set; zeroes g.
-__global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_params gr,
-                           smoe_params m, smoe_params v, float lr0, float lr1, float lr2,
-                           float lr3, Betas be, float bc1, float isb2) {
+// One launch over the groups of a SoA parameter set; zeroes g.
+__global__ void k_adam_soa(int64_t K, int C, int has_w, int has_pi, smoe_params p,
+                           smoe_params gr, smoe_params m, smoe_params v, float lr0, float lr1,
+                           float lr2, float lr3, float lr4, Betas be, float bc1, float isb2) {
     const int64_t n_mu = 2 * K, n_ch = 3 * K, n_ea = (int64_t)C * K;
     const int64_t n_w = has_w ? 2 * (int64_t)C * K : 0;
-    const int64_t total = n_mu + n_ch + n_ea + n_w;
+    const int64_t n_pi = has_pi ? K : 0;
+    const int64_t total = n_mu + n_ch + n_ea + n_w + n_pi;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         float *pp, *gg, *mm, *vv;
@@ -42,7 +43,8 @@ __global__ void k_adam_soa(int64_t K, int C, int has_w, smoe_params p, smoe_para
         if (x < n_mu) { pp = p.mu; gg = gr.mu; mm = m.mu; vv = v.mu; lr = lr0; }
         else if ((x -= n_mu) < n_ch) { pp = p.chol; gg = gr.chol; mm = m.chol; vv = v.chol; lr = lr1; }
         else if ((x -= n_ch) < n_ea) { pp = p.ea; gg = gr.ea; mm = m.ea; vv = v.ea; lr = lr2; }
-        else { x -= n_ea; pp = p.eW; gg = gr.eW; mm = m.eW; vv = v.eW; lr = lr3; }
+        else if ((x -= n_ea) < n_w) { pp = p.eW; gg = gr.eW; mm = m.eW; vv = v.eW; lr = lr3; }
+        else { x -= n_w; pp = p.logpi; gg = gr.logpi; mm = m.logpi; vv = v.logpi; lr = lr4; }
         AdamK k{be, lr / bc1, isb2};
         float pv = pp[x], mv = mm[x], vv_ = vv[x];
         adam1(pv, gg[x], mv, vv_, k);
@@ -70,6 +72,7 @@ __device__ void adam_coefs(const Geo &g, const int32_t *step, double b1, double 
         c[2] = (float)(im.lr_ea / bc1);
         c[3] = (float)(im.lr_eW / bc1);
         c[4] = (float)(1.0 / sqrt(1.0 - pow(b2, t)));
+        c[5] = (float)(im.lr_pi / bc1);
     }
 }
 
@@ -112,6 +115,7 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
             AdamK kch{be, cf[1], isb2};
             AdamK kea{be, cf[2], isb2};
             AdamK kew{be, cf[3], isb2};
+            AdamK kpi{be, cf[5], isb2};
             float gmx = 0.f, gmy = 0.f;
             if (rc.x <= rc.z) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
             for (int ch = 0; ch < C; ++ch) {
@@ -142,6 +146,11 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
                 float pv = chol[3 * kl + d], mv = m_chol[3 * kl + d], vv = v_chol[3 * kl + d];
                 adam1(pv, -s[d], mv, vv, kch);
                 chol[3 * kl + d] = pv; m_chol[3 * kl + d] = mv; v_chol[3 * kl + d] = vv;
+            }
+            if (im.p.logpi) {                              // gate weight: dL/dlogpi = S0
+                float pv = im.p.logpi[kl], mv = im.m.logpi[kl], vv = im.v.logpi[kl];
+                adam1(pv, s[5 + C * E], mv, vv, kpi);
+                im.p.logpi[kl] = pv; im.m.logpi[kl] = mv; im.v.logpi[kl] = vv;
             }
             if (!w.part)
                 for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
@@ -190,18 +199,20 @@ __global__ void k_sq_error(const float *y, const float *t, int64_t n, int clamp,
 }  // namespace
 
 cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
-                            const smoe_params &v, int C, const float lr[4], double b1, double b2,
+                            const smoe_params &v, int C, const float lr[5], double b1, double b2,
                             double eps, int32_t step, cudaStream_t st) {
     const int has_w = p.eW != nullptr;
-    const int64_t total = p.K * (5 + (int64_t)C * (has_w ? 3 : 1));
+    const int has_pi = p.logpi != nullptr;
+    const int64_t total = p.K * (5 + (int64_t)C * (has_w ? 3 : 1) + has_pi);
     if (total == 0) return cudaSuccess;
     const double bc1 = 1.0 - std::pow((double)b1, (double)step);
     const double isb2 = 1.0 / std::sqrt(1.0 - std::pow((double)b2, (double)step));
     int64_t blocks = (total + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
-    k_adam_soa<<<(unsigned)blocks, 256, 0, st>>>(p.K, C, has_w, p, gr, m, v, lr[0], lr[1],
-                                                 lr[2], lr[3], be, (float)bc1, (float)isb2);
+    k_adam_soa<<<(unsigned)blocks, 256, 0, st>>>(p.K, C, has_w, has_pi, p, gr, m, v, lr[0],
+                                                 lr[1], lr[2], lr[3], lr[4], be, (float)bc1,
+                                                 (float)isb2);
     return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ bool desc_ok(const smoe_desc *d) {
     if (d->C != 1 && d->C != 3) return false;
     if (d->tile != 8 && d->tile != 16 && d->tile != 32) return false;
     if (d->expert != 0 && d->expert != 1) return false;
+    if (d->gate != 0 && d->gate != 1) return false;
     if (!(d->qmax > 0.0f) || !(d->qmax <= kMaxQmax)) return false;
     if (!(d->scale > 0.0f) || !std::isfinite(d->scale)) return false;
     if (tiles_of(d->W, d->H, d->tile) > kMaxTiles) return false;
@@ -86,6 +87,7 @@ Geo make_geo(const smoe_desc *d, int64_t K) {
     g.linear = d->expert;
     g.S = rec_stride(d->C, d->expert);
     g.GS = acc_stride(d->C, d->expert);
+    g.rbf = d->gate;
     g.qmax = d->qmax;
     g.scale = d->scale;
     g.B = 1;
@@ -132,6 +134,7 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
     if (bt->C != 1 && bt->C != 3) return false;
     if (bt->tile != 8 && bt->tile != 16 && bt->tile != 32) return false;
     if (bt->expert != 0 && bt->expert != 1) return false;
+    if (bt->gate != 0 && bt->gate != 1) return false;
     if (!(bt->qmax > 0.0f) || !(bt->qmax <= kMaxQmax) || !bt->step) return false;
     if (bt->loss && bt->hist <= 0) return false;
     int64_t K_total = 0, t_total = 0;
@@ -144,6 +147,7 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
             if (q->K != im.p.K) return false;
             if (q->K > 0 && (!q->mu || !q->chol || !q->ea)) return false;
             if (q->K > 0 && ((q->eW != nullptr) != (bt->expert == 1))) return false;
+            if (q->K > 0 && ((q->logpi != nullptr) != (im.p.logpi != nullptr))) return false;
         }
         ImgDev &d = (*tab)[b];
         d.W = im.W;
@@ -163,6 +167,7 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
         d.lr_chol = im.lr_chol;
         d.lr_ea = im.lr_ea;
         d.lr_eW = im.lr_eW;
+        d.lr_pi = im.lr_pi;
         if (!(d.lr_mu0 > 0.0f)) d.lr_mu0 = d.lr_mu1 = 0.0f;
         K_total += im.p.K;
         t_total += (int64_t)d.tiles_x * d.tiles_y;
@@ -175,6 +180,7 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
     G.linear = bt->expert;
     G.S = rec_stride(bt->C, bt->expert);
     G.GS = acc_stride(bt->C, bt->expert);
+    G.rbf = bt->gate;
     G.qmax = bt->qmax;
     G.scale = 1.0f;
     G.B = bt->B;
@@ -264,11 +270,12 @@ smoe_status smoe_adam_step(const smoe_params *p, const smoe_params *g, const smo
                            double b2, double eps, int32_t step, void *stream) {
     if (!p || !g || !m || !v || !lr || step < 1 || (C != 1 && C != 3)) return SMOE_ERR_ARG;
     const smoe_params *all[4] = {p, g, m, v};
-    const bool has_w = p->eW != nullptr;
+    const bool has_w = p->eW != nullptr, has_pi = p->logpi != nullptr;
     for (const smoe_params *x : all) {
         if (x->K != p->K || x->K < 0) return SMOE_ERR_ARG;
         if (x->K > 0 && (!x->mu || !x->chol || !x->ea)) return SMOE_ERR_ARG;
         if ((x->eW != nullptr) != has_w) return SMOE_ERR_ARG;
+        if ((x->logpi != nullptr) != has_pi) return SMOE_ERR_ARG;
     }
     return cuda_status(launch_adam_soa(*p, *g, *m, *v, C, lr, b1, b2, eps, step,
                                        static_cast<cudaStream_t>(stream)));
@@ -338,6 +345,8 @@ smoe_status smoe_fit_init(const smoe_fit_batch *batch, const smoe_fit_image *img
                 if (e == cudaSuccess) e = cudaMemsetAsync(x->ea, 0, sizeof(float) * g.C * K, st);
                 if (e == cudaSuccess && x->eW)
                     e = cudaMemsetAsync(x->eW, 0, sizeof(float) * 2 * g.C * K, st);
+                if (e == cudaSuccess && x->logpi)
+                    e = cudaMemsetAsync(x->logpi, 0, sizeof(float) * K, st);
             }
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(batch->step, 0, sizeof(int32_t) * g.B, st);

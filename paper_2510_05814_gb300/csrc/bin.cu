@@ -87,7 +87,9 @@ __global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
     }
     if (valid) {
         float *r = w.rec + k * g.S;
-        r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c; r[5] = 0.0f; r[6] = 0.0f;
+        r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c;
+        r[5] = im.p.logpi ? __fmul_rn(im.p.logpi[kl], kLog2e) : 0.0f;   // log2 pi
+        r[6] = 0.0f;
         const int E = g.linear ? 3 : 1;
         for (int ch = 0; ch < g.C; ++ch) {
             r[7 + ch * E] = im.p.ea[kl * g.C + ch];

@@ -26,16 +26,19 @@
 // kernel's sums in shared memory, and after the chunk one float4 atomic per 4
 // sums per (tile, kernel) goes to the global accumulator.
 //
-// Raw per-kernel sums (s = g sum_c G_c (m_c - y_c), g = e / D, H_c = G_c / D,
-// so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c):
+// Raw per-kernel sums (e = pi exp(-q/2); s = g sum_c G_c (m_c - y_c), g = e / D,
+// H_c = G_c / D, so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c;
+// in the RBF mode of Eq. 1 (y = N, D = 1) the same holds with H_c = G_c and
+// the y term dropped):
 //   [0] A1 = sum s z0 dx  [1] B1 = sum s z0 dy  [2] C1 = sum s z1 dy
 //   [3] A2 = sum s z0     [4] Z3 = sum s z1
 //   [5+c] E_c = sum e H_c,   linear: [5+C+c] F_c = sum e H_c dx,
 //                                    [5+2C+c] Fy_c = sum e H_c dy
+//   [5+C*E] S0 = sum s
 // and the gradients (chain rule of Eqs. 2-4):
 //   dL/da = -A1, dL/db = -B1, dL/dc = -C1,
 //   dL/dmx = a A2 - sum_c W_c0 E_c,  dL/dmy = b A2 + c Z3 - sum_c W_c1 E_c,
-//   dL/dea_c = E_c, dL/dW_c0 = F_c, dL/dW_c1 = Fy_c.
+//   dL/dea_c = E_c, dL/dW_c0 = F_c, dL/dW_c1 = Fy_c, dL/dlogpi = S0.
 #include "smoe_internal.cuh"
 
 namespace smoe {
@@ -59,7 +62,8 @@ struct Rec {
     static constexpr int E = LIN ? 3 : 1;
     static constexpr int S = (7 + C * E + 3) & ~3;        // global record stride (floats)
     static constexpr int SS = (S % 8 == 0) ? S + 4 : S;   // shared stride: spreads banks
-    static constexpr int GS = (5 + C * E + 3) & ~3;       // accumulator stride (raw sums)
+    static constexpr int PI = 5 + C * E;                  // sum slot of dL/dlogpi
+    static constexpr int GS = (PI + 1 + 3) & ~3;          // accumulator stride (raw sums)
 };
 
 template <int C, int T>
@@ -178,7 +182,8 @@ __device__ __forceinline__ void fwd_pair(const float *r, float y0, float2 x2, fl
     const float2 dx = __fadd2_rn(x2, f2(-mx));
     const float2 z0 = __ffma2_rn(f2(a), dx, f2(t));
     const float2 q = __ffma2_rn(z0, z0, f2(u));
-    const float2 arg = __fmul2_rn(q, f2(kNegHalfLog2e));
+    // log2 of pi exp(-q/2): one FMA (pi = 1 stores 0, giving the plain product)
+    const float2 arg = __ffma2_rn(q, f2(kNegHalfLog2e), f2(r1.y));
     float2 e = make_float2(ex2(arg.x), ex2(arg.y));
     e.x = q.x <= qmax ? e.x : 0.0f;
     e.y = q.y <= qmax ? e.y : 0.0f;
@@ -332,9 +337,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(const __grid_co
             if (xi >= ti.W) continue;
             const float D = h ? Dv[bi].y : Dv[bi].x;
             const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+            const float sc = g.rbf ? 1.0f : inv;          // Eq. 1 does not normalise
             const int64_t o = (int64_t)yi * ti.W + xi;
 #pragma unroll
-            for (int ch = 0; ch < C; ++ch) y[ch * HW + o] = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * inv;
+            for (int ch = 0; ch < C; ++ch) y[ch * HW + o] = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * sc;
             if (inv_d) inv_d[o] = inv;
         }
     }
@@ -367,8 +373,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_mean(const __gr
         fwd_tile<C, LIN, T>(g, w, ti, sm, Dv, Nv);
 #pragma unroll
         for (int bi = 0; bi < G::BPW; ++bi) {
-            const float ia = Dv[bi].x > 0.0f ? 1.0f / Dv[bi].x : 0.0f;
-            const float ib = Dv[bi].y > 0.0f ? 1.0f / Dv[bi].y : 0.0f;
+            const float ia = g.rbf ? 1.0f : (Dv[bi].x > 0.0f ? 1.0f / Dv[bi].x : 0.0f);
+            const float ib = g.rbf ? 1.0f : (Dv[bi].y > 0.0f ? 1.0f / Dv[bi].y : 0.0f);
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
                 Sv[bi][ch].x = __fadd_rn(Sv[bi][ch].x, __fmul_rn(Nv[bi][ch].x, ia));
@@ -496,7 +502,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             }
             BwdAcc<C, LIN> acc;
             acc.zero();
-            const float2 nmx = f2(-mx), a2 = f2(a);
+            const float2 nmx = f2(-mx), a2 = f2(a), lp2 = f2(v[5]);
             uint32_t rows = __reduce_or_sync(0xffffffffu, m);
             while (rows) {
                 const int r = __ffs(rows) - 1;
@@ -536,7 +542,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                     const float2 dx = __fadd2_rn(x2, nmx);
                     const float2 z0 = __ffma2_rn(a2, dx, t2);
                     const float2 q = __ffma2_rn(z0, z0, u2);
-                    const float2 arg = __fmul2_rn(q, k2);
+                    const float2 arg = __ffma2_rn(q, k2, lp2);
                     float2 e = make_float2(ex2(arg.x), ex2(arg.y));
                     e.x = q.x <= qm ? e.x : 0.0f;
                     e.y = q.y <= qm ? e.y : 0.0f;
@@ -564,6 +570,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                 acc.v[2] = fmaf(z1 * dy, ss, acc.v[2]);
                 acc.v[3] += a2s;
                 acc.v[4] = fmaf(z1, ss, acc.v[4]);
+                acc.v[R::PI] += ss;
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     const float es = rE[ch].x + rE[ch].y;
@@ -625,13 +632,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_bwd(const __gri
             for (int ch = 0; ch < C; ++ch) H[h][ch] = 0.0f;
             if (xi < ti.W && yi < ti.H) {
                 const int64_t o = (int64_t)yi * ti.W + xi;
-                const float inv = inv_d[o];
+                const float inv = g.rbf ? 1.0f : inv_d[o];   // Eq. 1: D = 1, no y term
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     const float yv = y[ch * HW + o];
                     const float Gv = gy ? gy[ch * HW + o] : norm * (yv - target[ch * HW + o]);
                     H[h][ch] = inv * Gv;
-                    nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
+                    if (!g.rbf) nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
                 }
             }
         }
@@ -671,14 +678,15 @@ __device__ __forceinline__ void fit_tile_body(const Geo &g, const Bufs &w, int64
             if (xi < ti.W && yi < ti.H) {
                 const int64_t o = (int64_t)yi * ti.W + xi;
                 const float D = h ? Dv[bi].y : Dv[bi].x;
-                const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+                // softmax gates: y = N / D; RBF sum (Eq. 1): y = N and D = 1
+                const float inv = g.rbf ? 1.0f : (D > 0.0f ? 1.0f / D : 0.0f);
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     const float yv = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * inv;
                     const float d = yv - im.target[ch * HW + o];
                     se = fmaf(d, d, se);
                     H[h][ch] = inv * (norm * d);
-                    nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
+                    if (!g.rbf) nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);
                 }
             }
         }
@@ -756,6 +764,7 @@ __global__ void k_finalize(const __grid_constant__ Geo g, Bufs w, smoe_params gr
     grad.chol[3 * k] += -s[0] / g.scale;
     grad.chol[3 * k + 1] += -s[1] / g.scale;
     grad.chol[3 * k + 2] += -s[2] / g.scale;
+    if (grad.logpi) grad.logpi[k] += s[5 + C * E];
 }
 
 // Raise a tile kernel's dynamic shared-memory limit once per instantiation.

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
     int64_t n, const int64_t *__restrict__ n_in, const float2 *__restrict__ xy,
     const int32_t *__restrict__ order, const int32_t *__restrict__ pt_tile,
     const int32_t *__restrict__ tile_off, const int32_t *__restrict__ pair_k,
-    const float *__restrict__ rec, int S, float qmax, float *__restrict__ y,
+    const float *__restrict__ rec, int S, float qmax, int rbf, float *__restrict__ y,
     float *__restrict__ inv_d, const int32_t *status) {
     constexpr int E = LIN ? 3 : 1;
     if (status_bad(status)) return;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
     for (int32_t q = tile_off[t]; q < e; ++q) {
         const float *r = rec + (int64_t)pair_k[q] * S;
         const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
-        const float c = __ldg(r + 4);
+        const float c = __ldg(r + 4), lp = __ldg(r + 5);
         const float dx = __fsub_rn(p.x, r0.x);
         const float dy = __fsub_rn(p.y, r0.y);
         const float tb = __fmul_rn(r0.w, dy);
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
         float z0;
         const float qv = q_of(r0.z, dx, tb, u, z0);
         if (!(qv <= qmax)) continue;
-        const float ev = ex2(__fmul_rn(qv, kNegHalfLog2e));
+        const float ev = ex2(__fmaf_rn(qv, kNegHalfLog2e, lp));     // pi exp(-q/2)
         D += ev;
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) {
@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
         }
     }
     const float inv = D > 0.0f ? 1.0f / D : 0.0f;
+    const float sc = rbf ? 1.0f : inv;                // Eq. 1 does not normalise
 #pragma unroll
-    for (int ch = 0; ch < C; ++ch) y[ch * n + i] = N[ch] * inv;
+    for (int ch = 0; ch < C; ++ch) y[ch * n + i] = N[ch] * sc;
     if (inv_d) inv_d[i] = inv;
 }
 
@@ -114,9 +115,11 @@ template <int C, bool LIN>
 void launch_points_kernel(unsigned grid, cudaStream_t st, int64_t n, const int64_t *n_in,
                           const float2 *xy, const int32_t *order, const int32_t *pt_tile,
                           const int32_t *tile_off, const int32_t *pair_k, const float *rec,
-                          int S, float qmax, float *y, float *inv_d, const int32_t *status) {
+                          int S, float qmax, int rbf, float *y, float *inv_d,
+                          const int32_t *status) {
     k_render_points<C, LIN><<<grid, kPtThreads, 0, st>>>(n, n_in, xy, order, pt_tile, tile_off,
-                                                         pair_k, rec, S, qmax, y, inv_d, status);
+                                                         pair_k, rec, S, qmax, rbf, y, inv_d,
+                                                         status);
 }
 
 }  // namespace
@@ -148,16 +151,16 @@ cudaError_t launch_render_points(const Geo &g, const float *rec, const int32_t *
     const int S = g.S;
     if (g.C == 1 && !g.linear)
         launch_points_kernel<1, false>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
-                                       pair_k, rec, S, g.qmax, y, inv_d, status);
+                                       pair_k, rec, S, g.qmax, g.rbf, y, inv_d, status);
     else if (g.C == 1)
         launch_points_kernel<1, true>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
-                                      pair_k, rec, S, g.qmax, y, inv_d, status);
+                                      pair_k, rec, S, g.qmax, g.rbf, y, inv_d, status);
     else if (!g.linear)
         launch_points_kernel<3, false>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
-                                       pair_k, rec, S, g.qmax, y, inv_d, status);
+                                       pair_k, rec, S, g.qmax, g.rbf, y, inv_d, status);
     else
         launch_points_kernel<3, true>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,
-                                      pair_k, rec, S, g.qmax, y, inv_d, status);
+                                      pair_k, rec, S, g.qmax, g.rbf, y, inv_d, status);
     return cudaGetLastError();
 }
 

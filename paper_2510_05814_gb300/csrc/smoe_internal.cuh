@@ -7,12 +7,13 @@
 //     every tile kernel with one contiguous load): S floats,
 //       [0] mx  [1] my   centre in output pixels (float product mu * W)
 //       [2] a   [3] b  [4] c   L / s
-//       [5] [6] spare
+//       [5] log2(e) * logpi (the gate weight pi = exp(logpi), Eq. 4; 0 for pi = 1)
+//       [6] spare
 //       [7 + c*E + 0] ea_c, [7 + c*E + 1] eW_c0 / s, [7 + c*E + 2] eW_c1 / s
 //     with E = 3 for linear and 1 for constant experts, S = round_up(7+C*E, 4)
 //     (16 floats = 64 B for RGB linear experts);
 //   - backward accumulator per kernel: GS floats of raw per-kernel sums
-//     (see render.cu), GS = round_up(5 + C*E, 4);
+//     (see render.cu), GS = round_up(6 + C*E, 4);
 //   - tile lists: CSR tile_off / pair_k over the global tile index of a batch
 //     (image b's tiles start at t_off, row-major inside the image).
 #pragma once
@@ -25,6 +26,7 @@ namespace smoe {
 
 constexpr int kMaxC = 3;
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
+constexpr float kLog2e = 1.44269504088896340736f;
 
 // One image of a launch.  Its kernels have global ids [k_off, k_off + K) and
 // its tiles [t_off, t_off + tiles_x * tiles_y); p / m / v are the image's own
@@ -35,11 +37,12 @@ struct ImgDev {
     const float *target;
     smoe_params p, m, v;
     int32_t iters;
-    float lr_mu0, lr_mu1, lr_chol, lr_ea, lr_eW;
+    float lr_mu0, lr_mu1, lr_chol, lr_ea, lr_eW, lr_pi;
 };
 
 struct Geo {
     int32_t C, T, linear, S, GS;
+    int32_t rbf;           // 1: RBF sum of Eq. 1 (y = N, D = 1); 0: softmax gates (Eq. 4)
     float qmax, scale;
     int32_t B;
     int64_t K_total, tiles_total;
@@ -93,7 +96,7 @@ __host__ __device__ inline int rec_stride(int C, int linear) {
     return (7 + C * (linear ? 3 : 1) + 3) & ~3;
 }
 __host__ __device__ inline int acc_stride(int C, int linear) {
-    return (5 + C * (linear ? 3 : 1) + 3) & ~3;
+    return (6 + C * (linear ? 3 : 1) + 3) & ~3;
 }
 
 __device__ __forceinline__ const ImgDev &img_of(const Geo &g, int b) {
@@ -182,7 +185,7 @@ cudaError_t launch_render_bwd(const Geo &g, const Bufs &w, const float *y, const
 cudaError_t launch_fit_tiles(const Geo &g, const Bufs &w, double *loss, int32_t hist,
                              const int32_t *step, bool persistent, cudaStream_t st);
 cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const smoe_params &m,
-                            const smoe_params &v, int C, const float lr[4], double b1, double b2,
+                            const smoe_params &v, int C, const float lr[5], double b1, double b2,
                             double eps, int32_t step, cudaStream_t st);
 cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, double eps,
                             int32_t *step, uint32_t *done, float *coef, cudaStream_t st);

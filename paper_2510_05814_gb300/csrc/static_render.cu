@@ -70,6 +70,7 @@ extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smo
     if (!d || !p || !y || !status) return SMOE_ERR_ARG;
     if (d->W <= 0 || d->H <= 0 || (d->C != 1 && d->C != 3) ||
         (d->tile != 8 && d->tile != 16 && d->tile != 32) || (d->expert != 0 && d->expert != 1) ||
+        (d->gate != 0 && d->gate != 1) ||
         !(d->qmax > 0.0f) || !(d->scale > 0.0f) || !std::isfinite(d->scale))
         return SMOE_ERR_ARG;
     if (p->K < 0 || (p->K > 0 && (!p->mu || !p->chol || !p->ea)) ||
@@ -93,6 +94,7 @@ extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smo
     g.linear = d->expert;
     g.S = rec_stride(d->C, d->expert);
     g.GS = acc_stride(d->C, d->expert);
+    g.rbf = d->gate;
     g.qmax = d->qmax;
     g.scale = d->scale;
     g.B = 1;

@@ -20,7 +20,9 @@ class FitBatch:
 
     targets: list of (C,H,W) float32 CUDA tensors; params: list of SMoEParams
     (each image's own tensors, updated in place); iters: per-image run length
-    (int or list); lr = (mu0, mu1, chol, ea, eW) or one tuple per image;
+    (int or list); lr = (mu0, mu1, chol, ea, eW[, pi]) or one tuple per image
+    (pi: the rate of the gate weights log pi_k, for parameters that carry them);
+    rbf: fit the unnormalised RBF sum of Eq. 1 instead of the softmax gates;
     persistent: run the fused tile kernel as one persistent grid;
     deterministic: per-pair gradient partials added in a fixed order (a fit
     is then bit-reproducible and independent of the rest of the batch)."""
@@ -28,7 +30,7 @@ class FitBatch:
     def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
                  qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
                  persistent=False, pair_cap=None, moments=None, steps=None,
-                 deterministic=False, device="cuda"):
+                 deterministic=False, device="cuda", rbf=False):
         """moments: optional list of (m, v) SMoEParams per image and steps an
         optional list of iterations already done: a run that continues in a
         re-formed batch keeps its Adam state and schedule position."""
@@ -40,6 +42,7 @@ class FitBatch:
         self.tile, self.qmax = tile, qmax
         self.b1, self.b2, self.eps = b1, b2, eps
         self.persistent = bool(persistent)
+        self.rbf = bool(rbf)
         self.deterministic = bool(deterministic)
         self.targets = [t.contiguous() for t in targets]
         self.iters = [iters] * self.B if np.isscalar(iters) else list(iters)
@@ -79,10 +82,10 @@ class FitBatch:
             lr = self.lr[b]
             imgs[b] = _lib.FitImage(t.shape[2], t.shape[1], _ptr(t), self.params[b].c(),
                                     self.m[b].c(), self.v[b].c(), int(self.iters[b]), lr[0],
-                                    lr[1], lr[2], lr[3], lr[4])
+                                    lr[1], lr[2], lr[3], lr[4], lr[5] if len(lr) > 5 else 0.0)
         batch = _lib.FitBatch(self.B, self.C, self.tile, int(self.linear), self.qmax, self.b1,
                               self.b2, self.eps, _ptr(self.step), _ptr(self.loss), self.hist,
-                              int(self.persistent), int(self.deterministic))
+                              int(self.persistent), int(self.deterministic), int(self.rbf))
         return batch, imgs
 
     def _setup(self, reset):

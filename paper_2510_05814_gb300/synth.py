@@ -167,6 +167,7 @@ class Params:
     chol: np.ndarray         # (K, 3)
     ea: np.ndarray           # (K, C)
     eW: np.ndarray | None    # (K, C, 2) or None
+    logpi: np.ndarray | None = None   # (K,) gate weights log pi_k, or None (pi = 1)
 
     @property
     def K(self):
@@ -174,7 +175,8 @@ class Params:
 
     def copy(self):
         return Params(self.mu.copy(), self.chol.copy(), self.ea.copy(),
-                      None if self.eW is None else self.eW.copy())
+                      None if self.eW is None else self.eW.copy(),
+                      None if self.logpi is None else self.logpi.copy())
 
 
 def init_params(target, K, sigma, linear, seed, aniso=None, slope_std=0.0, offset=(0.0, 0.0)):

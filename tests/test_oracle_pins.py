@@ -852,3 +852,30 @@ def test_fit_with_gate_weights_decreases_loss(om):
     loss = om.fit(m, t, 15, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2, 5e-2))
     assert loss[-1] < 0.9 * loss[0]
     assert np.abs(m.logpi).max() > 1e-3            # the weights moved
+
+
+def test_render_term_scale_bounds_the_render(om):
+    """The render's term scale (used for the parity tolerance) bounds |y| by
+    the triangle inequality, equals y for non-negative constant experts, and
+    exceeds |y| where a linear expert cancels its offset."""
+    rng = np.random.default_rng(90)
+    m = rand_model(om, rng, W=20, H=18, K=8, linear=True)
+    y, _, s = om.render(m, with_scale=True)
+    assert np.all(np.abs(y) <= s * (1 + 1e-12))
+    c = rand_model(om, rng, W=20, H=18, K=8, linear=False)
+    yc, _, sc = om.render(c, with_scale=True)
+    np.testing.assert_allclose(sc, yc, rtol=1e-12, atol=0)
+    one = om.Model(16, 16, 1, np.array([[0.5, 0.5]]), np.array([[0.3, 0.0, 0.3]]),
+                   np.array([[0.0]]), np.array([[[0.1, 0.0]]]))
+    y1, _, s1 = om.render(one, with_scale=True)
+    # m(x) = 0.1 (x - 8): at x = 8.5 the value is 0.05 and the scale 0.05, at
+    # x = 0.5 (m = -0.75) both 0.75: with a zero offset the scale is |m|
+    np.testing.assert_allclose(s1[0, 8], np.abs(y1[0, 8]), rtol=1e-12)
+    rng2 = np.random.default_rng(91)
+    m2 = rand_model(om, rng2, W=20, H=18, K=1, linear=True)
+    m2.ea[:] = 1.0
+    m2.eW[:] = 0.0
+    m2.eW[0, :, 0] = 0.2
+    y2, _, s2 = om.render(m2, with_scale=True)
+    cov = s2 > 0
+    assert np.any(s2[cov] > np.abs(y2[cov]) * (1 + 1e-9))   # cancelling pixels
