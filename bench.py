@@ -363,6 +363,80 @@ def run_denoise(args):
     }), flush=True)
 
 
+def run_quality(args):
+    """Fit quality and speed on the paper-shaped workloads: the 128x128 grey
+    image (K = 256, constant experts, 100 iterations at lr 1e-2) and the
+    512x512 RGB image (K = 16384, linear experts, 2000 iterations at the
+    paper's rates) as softmax-gated R-SMoE (Eq. 4) and with learned gate
+    weights pi_k; then softmax gates against the unnormalised RBF sum of
+    Eq. 1 (the Gaussian-splatting regression the paper compares against)
+    with constant experts at equal kernel counts.  PSNR against the target; iterations/s from CUDA events
+    over graph replays of 25 iterations."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import api, build, synth
+    from paper_2510_05814_gb300.fit import FitBatch
+    build.build()
+
+    def psnr(y, t):
+        mse = float(((y.clamp(0.0, 1.0) - t) ** 2).mean())
+        return 10.0 * np.log10(1.0 / mse)
+
+    def one(name, target, params, iters, lr, rbf=False, pi=False):
+        C, H, W = target.shape
+        t = torch.tensor(target, device="cuda")
+        if pi:
+            params = synth.Params(params.mu, params.chol, params.ea, params.eW,
+                                  np.zeros(params.K, np.float32))
+        p = api.SMoEParams.from_numpy(params)
+        fb = FitBatch([t], [p], iters, lr=lr, tile=16, rbf=rbf)
+        chunk = 25 if iters % 25 == 0 else 1
+        fb.capture(chunk)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        # graph replays; a pair-buffer overflow (the lists grow as kernels
+        # widen) grows the buffer and resumes, inside the timed region
+        fb.run(iters, graph_iters=chunk, check_every=max(chunk, iters // 4))
+        e1.record()
+        torch.cuda.synchronize()
+        y, inv, _ = api.render(fb.params_of(0), W, H, tile=16, rbf=rbf)
+        s = e0.elapsed_time(e1) / 1e3
+        return {"run": name, "image": f"{W}x{H}x{C}", "K": params.K, "iters": iters,
+                "gate": "rbf (Eq. 1)" if rbf else ("softmax, learned pi" if pi else "softmax"),
+                "lr": list(lr), "psnr_db": psnr(y, t),
+                "uncovered_px": float((inv == 0).float().mean()),   # D = 0: y = 0, no gradient
+                "iters_per_s": iters / s, "s": s}
+
+    rows = []
+    g = synth.plain_gray_128()
+    rows.append(one("config 1: grey 128^2", g.target, g.params, 100, (1e-2,) * 5))
+    c2 = synth.rgb_512()
+    lr_pi = tuple(synth.PAPER_LR) + (1e-2,)
+    rows.append(one("config 2: RGB 512^2", c2.target, c2.params, 2000, synth.PAPER_LR))
+    rows.append(one("config 2, learned pi", c2.target, c2.params, 2000, lr_pi, pi=True))
+    # Sparsity comparison of Sec. II / VII: constant experts (the colours of a
+    # Gaussian-splatting model), softmax gates against the RBF sum at equal
+    # kernel counts, the paper's protocol of 10000 Adam iterations.  The RBF
+    # colours start at target x spacing^2 / (2 pi sigma^2), the inverse of the
+    # kernels' mean overlap on the grid, so that both start near the target.
+    # The rates: the paper's, and ten times its L / expert rates with a tenth
+    # of its centre rate (under the per-pixel cutoff, pixels that no kernel
+    # reaches get y = 0 and no gradient; the faster shape rates leave fewer).
+    fast = (1e-3, 1e-6, 1e-2, 1e-2, 1e-2)
+    for K in (4096, 16384):
+        pk = synth.init_params(c2.target, K, 5.0, False, 2)
+        overlap = (512 * 512 / K) / (2 * np.pi * 25.0)
+        pr = synth.Params(pk.mu, pk.chol, (pk.ea * min(1.0, overlap)).astype(np.float32), None)
+        for lr in (synth.PAPER_LR, fast):
+            rows.append(one(f"sparsity K={K}, SMoE", c2.target, pk, 10000, lr))
+            rows.append(one(f"sparsity K={K}, RBF", c2.target, pr, 10000, lr, rbf=True))
+    rows.append(one("config 2, fast rates", c2.target, c2.params, 10000, fast))
+    print(json.dumps({"metric": "fit PSNR and iterations/s on the paper-shaped workloads",
+                      "mode": "quality", "rows": rows, "data": "synthetic", "dtype": "f32"}),
+          flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals (50 req/s): fit requests (ragged sizes, half of them
     denoising with N(0, 0.05) noise, `iters` Adam steps) and render requests
@@ -410,9 +484,11 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--mode", default="fit", choices=["fit", "batched", "serve", "denoise"],
+    ap.add_argument("--mode", default="fit",
+                    choices=["fit", "batched", "serve", "denoise", "quality"],
                     help="fit: the 2048^2 fit step (default); batched: 64 ragged images; "
-                         "serve: Poisson request stream; denoise: MM-RSMoE")
+                         "serve: Poisson request stream; denoise: MM-RSMoE; quality: PSNR "
+                         "and iterations/s of configs 1-2, learned pi and the RBF mode")
     ap.add_argument("--models", type=int, nargs="+", default=[1, 8, 16, 64],
                     help="denoise: model counts H")
     ap.add_argument("--images", type=int, default=64)
@@ -431,6 +507,8 @@ def main():
     if args.mode == "serve":
         args.iters = args.iters or 500
         return run_serve(args)
+    if args.mode == "quality":
+        return run_quality(args)
     if args.mode == "denoise":
         args.iters = args.iters or 2000
         return run_denoise(args)

@@ -55,6 +55,9 @@ constexpr int kThreads = kNW * 32;
 #ifndef SMOE_NCH
 #define SMOE_NCH 256
 #endif
+#ifndef SMOE_FWD_UNROLL
+#define SMOE_FWD_UNROLL 4
+#endif
 constexpr int kMinBlocks = SMOE_MIN_BLOCKS;
 
 template <int C, bool LIN>
@@ -230,6 +233,15 @@ __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) N2[ch] = f2(0.0f);
     int i = 0;
+#if SMOE_FWD_UNROLL >= 4
+    // four kernels in flight: two pairs of accumulators, each pair fed twice
+    for (; i + 3 < cnt; i += 4) {
+        fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(sm.rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
+        fwd_pair<C, LIN>(sm.rec + lst[i + 2] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(sm.rec + lst[i + 3] * R::SS, y0, x2, qmax, D2, N2);
+    }
+#endif
     for (; i + 1 < cnt; i += 2) {
         fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
         fwd_pair<C, LIN>(sm.rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
