@@ -26,7 +26,7 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortMax = 2048;                 // bitonic in shared memory up to this
 constexpr int kBitmapWords = 8192;             // 262144 kernel ids per bitmap pass
-constexpr int kLongGrid = 608;                 // CTAs sweeping the queue of long lists
+constexpr int kLongGrid = 152;                 // CTAs sweeping the queue of long lists (> 1024 ids)
 
 // Add 1 to the count (or claim a slot) of every tile of the rectangles of
 // the warp's kernels.  Small rectangles are walked by their own lane; a large
@@ -46,10 +46,30 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
             atomicAdd(&w.tile_cnt[t], 1);
         }
     };
-    if (n <= kBig) {
-        for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
-            for (int tx = rect.x; tx <= rect.z; ++tx)
-                visit(t_off + (int64_t)ty * tiles_x + tx, k);
+    // Small rectangles, walked in step by the whole warp: at step i every lane
+    // takes the i-th tile of its own rectangle, and lanes that meet on one
+    // tile (neighbouring kernels overlap) share one atomic, taken by the
+    // lowest of them for the group's count.
+    const int n_small = n <= kBig ? n : 0;
+    int steps = n_small;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, o));
+    for (int i = 0; i < steps; ++i) {
+        const bool act = i < n_small;
+        const int64_t t = act ? t_off + (int64_t)(rect.y + i / wdt) * tiles_x + rect.x + i % wdt : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, t);
+        if (act) {
+            const int leader = __ffs(peers) - 1;
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            if (SCATTER) {
+                int base = 0;
+                if (lane == leader) base = atomicAdd(&w.cursor[t], __popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                w.pair_tmp[(int64_t)w.tile_off[t] + base + rank] = k;
+            } else if (lane == leader) {
+                atomicAdd(&w.tile_cnt[t], __popc(peers));
+            }
+        }
     }
     unsigned big = __ballot_sync(0xffffffffu, n > kBig);
     while (big) {
@@ -280,9 +300,61 @@ __device__ int block_exscan_int(int v, int *total) {
 
 __device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s);
 
-// One warp per tile: lists of up to 256 ids are sorted in registers (8 per
-// lane, bitonic network, lane-crossing stages by shuffles); longer lists are
-// queued for k_segsort_long.
+// Bitonic sort of the warp's 32 E ids in registers, ascending; element
+// p = lane E + i.  Compare-exchange stages whose partner is in another lane
+// (distance j >= E) go through shuffles, the others stay inside the lane.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane) {
+    constexpr int P = 32 * E;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= E) {
+                const int lj = j / E;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const bool up = ((lane * E + i) & k) == 0;
+                    const int o = __shfl_xor_sync(0xffffffffu, v[i], lj);
+                    v[i] = (lower == up) ? min(v[i], o) : max(v[i], o);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < E; ++i) {
+                    const int ip = i ^ j;
+                    if (ip > i) {
+                        const bool up = ((lane * E + i) & k) == 0;
+                        const int a = v[i], b = v[ip];
+                        v[i] = up ? min(a, b) : max(a, b);
+                        v[ip] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_list(const Bufs &w, int64_t start, int n, int lane) {
+    int v[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        v[i] = p < n ? w.pair_tmp[start + p] : 0x7fffffff;
+    }
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        if (p < n) w.pair_k[start + p] = v[i];
+    }
+}
+
+// One warp per tile: lists of up to kWarpSortMax ids are sorted in registers
+// (8, 16 or 32 per lane); longer lists are queued for k_segsort_long.
+constexpr int kWarpSortMax = 1024;
+
 __global__ void __launch_bounds__(256) k_segsort_warp(int64_t n_tiles, Bufs w) {
     if (status_bad(w.status)) return;
     const int lane = threadIdx.x & 31;
@@ -294,47 +366,14 @@ __global__ void __launch_bounds__(256) k_segsort_warp(int64_t n_tiles, Bufs w) {
         if (n == 1 && lane == 0) w.pair_k[start] = w.pair_tmp[start];
         return;
     }
-    if (n > 256) {
-        if (lane == 0) w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
-        return;
-    }
-    int v[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int p = lane * 8 + i;
-        v[i] = p < n ? w.pair_tmp[start + p] : 0x7fffffff;
-    }
-#pragma unroll
-    for (int k = 2; k <= 256; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 8) {
-                const int lj = j >> 3;
-                const bool lower = (lane & lj) == 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const bool up = ((lane * 8 + i) & k) == 0;
-                    const int o = __shfl_xor_sync(0xffffffffu, v[i], lj);
-                    v[i] = (lower == up) ? min(v[i], o) : max(v[i], o);
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int ip = i ^ j;
-                    if (ip > i) {
-                        const bool up = ((lane * 8 + i) & k) == 0;
-                        const int a = v[i], b = v[ip];
-                        v[i] = up ? min(a, b) : max(a, b);
-                        v[ip] = up ? max(a, b) : min(a, b);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int p = lane * 8 + i;
-        if (p < n) w.pair_k[start + p] = v[i];
+    if (n <= 256) {
+        warp_sort_list<8>(w, start, n, lane);
+    } else if (n <= 512) {
+        warp_sort_list<16>(w, start, n, lane);
+    } else if (n <= kWarpSortMax) {
+        warp_sort_list<32>(w, start, n, lane);
+    } else if (lane == 0) {
+        w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
     }
 }
 

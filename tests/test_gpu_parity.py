@@ -190,6 +190,25 @@ def test_long_lists_use_bitmap_path():
         check_grad(a, b, name, t, rtol=1e-3)
 
 
+@pytest.mark.parametrize("K", [400, 700, 1500])
+def test_mid_length_lists_are_bitexact(K):
+    """Lists of 257-512 and 513-1024 ids take the warp register sorts with
+    16 and 32 ids per lane, longer ones the shared-memory sort: the lists
+    are still bit-exact and the render matches."""
+    p = rand_case(40 + K, 48, 48, 3, K, True, sig=(20.0, 30.0), span=(0.2, 0.8))
+    params, r = gpu_raster(p, 48, 48, 3, 16, 1.0)
+    off, pk = r.lists()
+    m = oracle_model(p, 48, 48, 3, 16)
+    ref_off, ref_pk = om.bin_tiles(m)
+    lens = np.diff(ref_off)
+    assert lens.max() > 256
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    y, _ = r.render()
+    ref, _, absm = om.render(m, with_scale=True)
+    check_y(y.cpu().numpy(), ref, absm, "y")
+
+
 def test_empty_model_and_offimage_kernels():
     p = synth.Params(np.array([[3.0, 3.0], [-2.0, 0.5]], np.float32),
                      np.array([[0.3, 0.0, 0.3], [0.3, 0.0, 0.3]], np.float32),
