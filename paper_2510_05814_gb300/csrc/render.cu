@@ -93,7 +93,7 @@ struct Smem {
     int32_t kid[G::NCH];
     uint8_t flist[kNW][G::NCH];          // per-warp compacted kernel list of a band
     uint8_t order[G::NCH];               // backward: kernels grouped by first row
-    int bcnt[T + 1], boff[T + 1];
+    int bcnt[2 * T], boff[2 * T];        // backward grouping buckets (2T - 1 keys)
     double lsum[kNW];
     long long next;                      // persistent launch: the CTA's next tile
 };
@@ -464,35 +464,40 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
         const int nc = min(G::NCH, ti.n - c0);
         __syncthreads();                          // previous users of the chunk are done
         if (!(staged && c0 == 0 && ti.n <= G::NCH)) stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
-        // Group the kernels by first row (counting sort; the order inside a
-        // group does not change any kernel's sums).
-        if (threadIdx.x <= T) sm.bcnt[threadIdx.x] = 0;
+        // Group the kernels by the centre of their row span, first + last row
+        // (counting sort over 2T - 1 keys), so that a warp's 32 kernels cover
+        // similar rows; kernels that miss every row are dropped.  The order
+        // inside a group does not change any kernel's sums.
+        constexpr int NB = 2 * T - 1;
+        if (threadIdx.x < 2 * T) sm.bcnt[threadIdx.x] = 0;
         __syncthreads();
         for (int j = threadIdx.x; j < nc; j += kThreads) {
             const uint32_t m = sm.mask[j];
-            if (m) atomicAdd(&sm.bcnt[__ffs(m) - 1], 1);
+            if (m) atomicAdd(&sm.bcnt[(__ffs(m) - 1) + (31 - __clz(m))], 1);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             int acc = 0;
-            for (int r = 0; r < T; ++r) {
+            for (int r = 0; r < NB; ++r) {
                 sm.boff[r] = acc;
                 acc += sm.bcnt[r];
                 sm.bcnt[r] = 0;
             }
-            sm.boff[T] = acc;
+            sm.boff[NB] = acc;
         }
         __syncthreads();
         for (int j = threadIdx.x; j < nc; j += kThreads) {
             const uint32_t m = sm.mask[j];
             if (m) {
-                const int r0 = __ffs(m) - 1;
-                sm.order[sm.boff[r0] + atomicAdd(&sm.bcnt[r0], 1)] = (uint8_t)j;
+                const int key = (__ffs(m) - 1) + (31 - __clz(m));
+                sm.order[sm.boff[key] + atomicAdd(&sm.bcnt[key], 1)] = (uint8_t)j;
             }
         }
         __syncthreads();
-        const int n_live = sm.boff[T];
-        for (int grp = warp; grp * 32 < n_live; grp += kNW) {
+        const int n_live = sm.boff[NB];
+        // One 32-kernel group: every lane walks its kernel over the rows in
+        // `rowsel` of the union of the group's row masks.
+        auto group = [&](int grp, uint32_t rowsel) {
             const int idx = grp * 32 + lane;
             const bool valid = idx < n_live;
             const int j = valid ? sm.order[idx] : 0;
@@ -515,7 +520,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             BwdAcc<C, LIN> acc;
             acc.zero();
             const float2 nmx = f2(-mx), a2 = f2(a), lp2 = f2(v[5]);
-            uint32_t rows = __reduce_or_sync(0xffffffffu, m);
+            uint32_t rows = __reduce_or_sync(0xffffffffu, m) & rowsel;
             while (rows) {
                 const int r = __ffs(rows) - 1;
                 rows &= rows - 1;
@@ -593,7 +598,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                     }
                 }
             }
-            if (m) {
+            if (m & rowsel) {
                 if (w.part) {        // deterministic: this pair's own slot
                     float4 *dst = reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS);
 #pragma unroll
@@ -608,7 +613,15 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                                                        acc.v[4 * q + 2], acc.v[4 * q + 3]));
                 }
             }
-        }
+        };
+        // Whole groups round-robin over the warps; with float atomics the
+        // n_groups mod kNW groups of the last round are shared by all warps,
+        // each taking the rows r = warp (mod kNW) and adding its own partial
+        // sums (the deterministic mode keeps whole groups: one writer per pair).
+        const int n_groups = (n_live + 31) >> 5;
+        const int whole = w.part ? n_groups : n_groups - n_groups % kNW;
+        for (int grp = warp; grp < whole; grp += kNW) group(grp, 0xffffffffu);
+        for (int grp = whole; grp < n_groups; ++grp) group(grp, 0x11111111u << warp);
         if (w.part) {                // pairs whose kernel misses every row add zero
             for (int i = threadIdx.x; i < nc * (R::GS / 4); i += kThreads) {
                 const int j = i / (R::GS / 4), q = i - j * (R::GS / 4);
