@@ -35,20 +35,22 @@ __global__ void k_pt_tile(int64_t n, const float2 *__restrict__ xy, int W, int H
                           float *__restrict__ inv_d, const int32_t *status) {
     if (status_bad(status)) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float2 p = xy[i];
+    const bool live = i < n;
+    const float2 p = live ? xy[i] : make_float2(-1.0f, -1.0f);
     int32_t t = -1;
     if (p.x >= 0.0f && p.x < (float)W && p.y >= 0.0f && p.y < (float)H) {
         // floor of a float in [0, W): exact integer conversion
         const int tx = min((int)p.x / T, tiles_x - 1);
         const int ty = (int)p.y / T;
         t = ty * tiles_x + tx;
-        atomicAdd(&cnt[t], 1);
-    } else {
+    } else if (live) {
         for (int ch = 0; ch < C; ++ch) y[ch * n + i] = 0.0f;
         if (inv_d) inv_d[i] = 0.0f;
     }
-    pt_tile[i] = t;
+    // neighbouring points mostly share a tile: one atomic per tile per warp
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    if (t >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[t], __popc(peers));
+    if (live) pt_tile[i] = t;
 }
 
 __global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
@@ -56,10 +58,14 @@ __global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
                              int32_t *__restrict__ order, const int32_t *status) {
     if (status_bad(status)) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int32_t t = pt_tile[i];
+    const int32_t t = i < n ? pt_tile[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
     if (t < 0) return;
-    order[off[t] + atomicAdd(&cursor[t], 1)] = (int32_t)i;
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&cursor[t], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    order[off[t] + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
 // One thread per sorted in-image point: D = sum e_k, N_c = sum e_k m_kc over
