@@ -46,30 +46,10 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
             atomicAdd(&w.tile_cnt[t], 1);
         }
     };
-    // Small rectangles, walked in step by the whole warp: at step i every lane
-    // takes the i-th tile of its own rectangle, and lanes that meet on one
-    // tile (neighbouring kernels overlap) share one atomic, taken by the
-    // lowest of them for the group's count.
-    const int n_small = n <= kBig ? n : 0;
-    int steps = n_small;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, o));
-    for (int i = 0; i < steps; ++i) {
-        const bool act = i < n_small;
-        const int64_t t = act ? t_off + (int64_t)(rect.y + i / wdt) * tiles_x + rect.x + i % wdt : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, t);
-        if (act) {
-            const int leader = __ffs(peers) - 1;
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            if (SCATTER) {
-                int base = 0;
-                if (lane == leader) base = atomicAdd(&w.cursor[t], __popc(peers));
-                base = __shfl_sync(peers, base, leader);
-                w.pair_tmp[(int64_t)w.tile_off[t] + base + rank] = k;
-            } else if (lane == leader) {
-                atomicAdd(&w.tile_cnt[t], __popc(peers));
-            }
-        }
+    if (n <= kBig) {             // small rectangles: each lane walks its own
+        for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
+            for (int tx = rect.x; tx <= rect.z; ++tx)
+                visit(t_off + (int64_t)ty * tiles_x + tx, k);
     }
     unsigned big = __ballot_sync(0xffffffffu, n > kBig);
     while (big) {
