@@ -538,13 +538,14 @@ def main():
 
     def pairs_now():
         r = api.Rasterizer(desc, params.K, pair_cap=fb.pair_cap).bin(fb.params_of(0))
-        return evaluated_pairs(r.tile_off.cpu().numpy(), W, H, T), int(r.n_pairs.item())
+        return (evaluated_pairs(r.tile_off.cpu().numpy(), W, H, T), int(r.n_pairs.item()),
+                r.count_inrange())
 
     for _ in range(args.warmup):
         fb.launch(1)
     torch.cuda.synchronize()
     assert fb.status_code() == 0
-    pairs0, lists0 = pairs_now()
+    pairs0, lists0, inrange0 = pairs_now()
     rates = issue_rates()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -573,8 +574,9 @@ def main():
     tile_ms = [e[1].elapsed_time(e[2]) for e in ev]
     adam_ms = [e[2].elapsed_time(e[3]) for e in ev]
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    pairs1, lists1 = pairs_now()
+    pairs1, lists1, inrange1 = pairs_now()
     pairs_step = 0.5 * (pairs0 + pairs1)
+    inrange_step = 0.5 * (inrange0 + inrange1)
     tot_s = sum(step_ms) / 1e3
 
     # end to end through the public API with host buffers: per step the
@@ -664,7 +666,8 @@ def main():
             "config": {"workload": WORKLOAD, "image": f"{W}x{H}x{C}", "K": params.K, "tile": T,
                        "l2": "flushed (256 MiB write, untimed) before every timed step",
                        "parallelism": f"replicas x{world}",
-                       "pairs_per_step": int(pairs_step), "list_pairs": int(lists1)},
+                       "pairs_per_step": int(pairs_step), "list_pairs": int(lists1),
+                       "in_range_pairs_per_step": int(inrange_step)},
             "roofline": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
                          "achieved": ex2_achieved / 1e9, "peak": ex2_peak / 1e9,
                          "unit": "Gex2/s", "frac": ex2_achieved / ex2_peak,
@@ -679,6 +682,10 @@ def main():
                              "issue_active": ncu["issue_active"],
                              "xu_active": ncu["xu_active"]}},
             "value_fwd_bwd_only": pairs_step / tile_s / 1e9,
+            # pairs with q <= q_max (the ones that contribute) per second of the
+            # fused tile kernel, and their share of the listed pairs
+            "in_range": {"Gpairs_per_s": inrange_step / tile_s / 1e9,
+                         "fraction_of_listed": inrange_step / pairs_step},
             "phases_ms": {"bin": statistics.mean(bin_ms), "fused_tiles": statistics.mean(tile_ms),
                           "adam": statistics.mean(adam_ms)},
             "fit_iters_per_s": args.steps / tot_s,

@@ -297,6 +297,16 @@ SMOE_API smoe_status smoe_render_points(const smoe_desc *d, int64_t K, const voi
                                         void *pws, size_t pws_bytes, float *y, float *inv_d,
                                         const int32_t *status, void *stream);
 
+/* Diagnostic: adds to *out (device, uint64) the number of (pixel, kernel)
+ * pairs of the lists whose kernel includes the pixel (q32 <= q_max, the
+ * truncation of Sec. IV), i.e. the pairs that contribute to the render, as
+ * against the listed pairs (sum over tiles of pixels x list length).  Same
+ * arguments as smoe_render; not part of the fit. */
+SMOE_API smoe_status smoe_count_inrange(const smoe_desc *d, int64_t K, const void *ws,
+                                        size_t ws_bytes, const int32_t *tile_off,
+                                        const int32_t *pair_k, uint64_t *out,
+                                        const int32_t *status, void *stream);
+
 /* Bin and render one model without allocating anything: for callers that
  * cannot call cudaMalloc (a plugin inside an application that owns every
  * device allocation, code that must not touch the allocator).  The paper has

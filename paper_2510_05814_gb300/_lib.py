@@ -15,7 +15,8 @@ EXPORTS = ["smoe_version", "smoe_workspace_size", "smoe_bin", "smoe_render",
            "smoe_render_backward", "smoe_adam_step", "smoe_sq_error",
            "smoe_fit_workspace_size", "smoe_fit_init", "smoe_fit", "smoe_fit_phase",
            "smoe_fit_render_mean", "smoe_sharpen", "smoe_points_workspace_size",
-           "smoe_render_points", "smoe_render_static", "smoe_get_status"]
+           "smoe_render_points", "smoe_count_inrange", "smoe_render_static",
+           "smoe_get_status"]
 
 
 class SmoeError(RuntimeError):
@@ -86,6 +87,7 @@ def load():
         "smoe_points_workspace_size": (I32, [D, I64, ctypes.POINTER(ctypes.c_size_t)]),
         "smoe_render_points": (I32, [D, I64, P, ctypes.c_size_t, P, P, I64, P, P,
                                      ctypes.c_size_t, P, P, P, P]),
+        "smoe_count_inrange": (I32, [D, I64, P, ctypes.c_size_t, P, P, P, P, P]),
         "smoe_render_static": (I32, [D, PP, P, P, P, P]),
         "smoe_get_status": (I32, [P, P]),
     }

@@ -248,6 +248,15 @@ class Rasterizer:
                                      _ptr(self.status), _stream(stream)), "smoe_render_points")
         return y, inv_d
 
+    def count_inrange(self, stream=None):
+        """Number of listed (pixel, kernel) pairs with q <= q_max (synchronises)."""
+        out = torch.zeros(1, dtype=torch.int64, device=self.device)
+        check(_lib.load().smoe_count_inrange(ctypes.byref(self.desc.c()), self.K, _ptr(self.ws),
+                                             self.ws.numel(), _ptr(self.tile_off),
+                                             _ptr(self.pair_k), _ptr(out), _ptr(self.status),
+                                             _stream(stream)), "smoe_count_inrange")
+        return int(out.item())
+
     def lists(self):
         """(tile_off, pair_k) trimmed to the pair count, on the host."""
         off = self.tile_off.cpu().numpy()

@@ -494,6 +494,19 @@ smoe_status smoe_render_points(const smoe_desc *d, int64_t K, const void *ws, si
                                             status, static_cast<cudaStream_t>(stream)));
 }
 
+smoe_status smoe_count_inrange(const smoe_desc *d, int64_t K, const void *ws, size_t ws_bytes,
+                               const int32_t *tile_off, const int32_t *pair_k, uint64_t *out,
+                               const int32_t *status, void *stream) {
+    if (!desc_ok(d) || K < 0 || K > 0x7fffffffLL || !tile_off || !out) return SMOE_ERR_ARG;
+    Geo g = make_geo(d, K);
+    const Layout L = layout(K, g.tiles_total, 0, g.S, g.GS, 1, false);
+    if (!ws_ok(ws, ws_bytes, L.total)) return SMOE_ERR_WORKSPACE;
+    const float *rec = reinterpret_cast<const float *>(static_cast<const char *>(ws) + L.rec);
+    return cuda_status(launch_count_inrange(g, rec, tile_off, pair_k,
+                                            reinterpret_cast<unsigned long long *>(out), status,
+                                            static_cast<cudaStream_t>(stream)));
+}
+
 smoe_status smoe_get_status(const int32_t *status, void *stream) {
     if (!status) return SMOE_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

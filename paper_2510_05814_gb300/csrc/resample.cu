@@ -128,7 +128,49 @@ void launch_points_kernel(unsigned grid, cudaStream_t st, int64_t n, const int64
                                                          status);
 }
 
+// In-range pairs: one CTA per tile, one thread per pixel of the tile; every
+// pixel tests the tile's whole list with the exact predicate and the CTA adds
+// its count of (pixel, kernel) pairs with q <= q_max to *out.
+__global__ void __launch_bounds__(1024) k_count_inrange(const __grid_constant__ Geo g,
+                                                        const float *__restrict__ rec,
+                                                        const int32_t *__restrict__ tile_off,
+                                                        const int32_t *__restrict__ pair_k,
+                                                        unsigned long long *out,
+                                                        const int32_t *status) {
+    if (status_bad(status)) return;
+    const int64_t t = blockIdx.x;
+    const int tiles_x = g.one.tiles_x;
+    const int x0 = (int)(t % tiles_x) * g.T, y0 = (int)(t / tiles_x) * g.T;
+    const int xi = x0 + (int)threadIdx.x % g.T, yi = y0 + (int)threadIdx.x / g.T;
+    unsigned long long n = 0;
+    if (xi < g.one.W && yi < g.one.H) {
+        const float px = (float)xi + 0.5f, py = (float)yi + 0.5f;
+        for (int32_t q = tile_off[t]; q < tile_off[t + 1]; ++q) {
+            const float *r = rec + (int64_t)pair_k[q] * g.S;
+            const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
+            const float c = __ldg(r + 4);
+            const float dx = __fsub_rn(px, r0.x), dy = __fsub_rn(py, r0.y);
+            const float z1 = __fmul_rn(c, dy);
+            float z0;
+            const float qv = q_of(r0.z, dx, __fmul_rn(r0.w, dy), __fmul_rn(z1, z1), z0);
+            n += qv <= g.qmax ? 1ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(out, n);
+}
+
 }  // namespace
+
+cudaError_t launch_count_inrange(const Geo &g, const float *rec, const int32_t *tile_off,
+                                 const int32_t *pair_k, unsigned long long *out,
+                                 const int32_t *status, cudaStream_t st) {
+    if (g.tiles_total == 0) return cudaSuccess;
+    k_count_inrange<<<(unsigned)g.tiles_total, g.T * g.T, 0, st>>>(g, rec, tile_off, pair_k, out,
+                                                                 status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_scale(const float *in, float *out, int64_t n, float f, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

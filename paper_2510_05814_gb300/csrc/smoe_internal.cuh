@@ -169,6 +169,10 @@ struct PointBufs {
     long long *bsum;
     int64_t *n_in;
 };
+// Adds to *out the number of (pixel, kernel) pairs of the lists with q <= q_max.
+cudaError_t launch_count_inrange(const Geo &g, const float *rec, const int32_t *tile_off,
+                                 const int32_t *pair_k, unsigned long long *out,
+                                 const int32_t *status, cudaStream_t st);
 // out = f * in elementwise (one rounding), n floats.
 cudaError_t launch_scale(const float *in, float *out, int64_t n, float f, cudaStream_t st);
 // y(x) of one model (g.B == 1) at n points xy (n x 2, pixel units of g.one's

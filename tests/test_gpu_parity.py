@@ -209,6 +209,17 @@ def test_mid_length_lists_are_bitexact(K):
     check_y(y.cpu().numpy(), ref, absm, "y")
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_count_inrange_matches_oracle(tile):
+    """The in-range pair count equals the number of (pixel, kernel) pairs
+    the oracle's predicate includes (every included pair is listed)."""
+    p = rand_case(50 + tile, 40, 30, 3, 25, True)
+    _, r = gpu_raster(p, 40, 30, 3, tile, 1.0)
+    m = oracle_model(p, 40, 30, 3, tile)
+    ref = sum(om.included(m, k, i, j) for k in range(m.K) for j in range(30) for i in range(40))
+    assert r.count_inrange() == ref
+
+
 def test_empty_model_and_offimage_kernels():
     p = synth.Params(np.array([[3.0, 3.0], [-2.0, 0.5]], np.float32),
                      np.array([[0.3, 0.0, 0.3], [0.3, 0.0, 0.3]], np.float32),
