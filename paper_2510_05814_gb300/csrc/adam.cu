@@ -82,11 +82,17 @@ __global__ void k_adam_coefs(const __grid_constant__ Geo g, const int32_t *step,
 }
 
 // Fit: raw per-kernel sums -> gradients (see render.cu) -> Adam on the 5 + C
-// (+ 2C) parameters of the kernel; zeroes the sums.  The last CTA to finish
-// advances every running image's step counter and forms the coefficients of
-// the next step.
+// (+ 2C, + 1 with gate weights) parameters of the kernel; zeroes the sums.
+// The sums and the prepared record are loaded whole (float4) into registers.
+// The last CTA to finish advances every running image's step counter and
+// forms the coefficients of the next step.
+template <int C, bool LIN>
 __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2,
                            Betas be, int32_t *step, uint32_t *done, float *coef) {
+    constexpr int E = LIN ? 3 : 1;
+    constexpr int S = (7 + C * E + 3) & ~3;       // record stride (floats)
+    constexpr int GS = (6 + C * E + 3) & ~3;      // sums stride (floats)
+    constexpr int PI = 5 + C * E;                 // dL/dlogpi slot
     if (status_bad(w.status)) return;
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k < g.K_total) {
@@ -95,65 +101,79 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
         const int32_t it = step[b];
         if (it < im.iters) {
             const int64_t kl = k - im.k_off;
-            float *mu = im.p.mu, *chol = im.p.chol, *ea = im.p.ea, *eW = im.p.eW;
-            float *m_mu = im.m.mu, *m_chol = im.m.chol, *m_ea = im.m.ea, *m_eW = im.m.eW;
-            float *v_mu = im.v.mu, *v_chol = im.v.chol, *v_ea = im.v.ea, *v_eW = im.v.eW;
             // A kernel listed in no tile touched no pixel: its gradient is 0
             // (and must not become inf * 0 for non-finite parameters).
             const int4 rc = w.rect[k];
-            float zero[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f,
-                              0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float *acc = w.acc + k * g.GS;
-            float gat[16];
-            if (w.part && rc.x <= rc.z) gather_sums(g, w, im, k, rc, gat);
-            const float *s = rc.x > rc.z ? zero : (w.part ? gat : acc);
-            const float *r = w.rec + k * g.S;
-            const int C = g.C, E = g.linear ? 3 : 1;
+            const bool listed = rc.x <= rc.z;
+            float s[GS];
+            float4 *acc = reinterpret_cast<float4 *>(w.acc + k * GS);
+            if (!listed) {
+#pragma unroll
+                for (int q = 0; q < GS; ++q) s[q] = 0.0f;
+            } else if (w.part) {
+                gather_sums<GS>(w, im, k, rc, s);
+            } else {
+#pragma unroll
+                for (int q = 0; q < GS / 4; ++q) {
+                    const float4 v = acc[q];
+                    s[4 * q] = v.x; s[4 * q + 1] = v.y; s[4 * q + 2] = v.z; s[4 * q + 3] = v.w;
+                }
+            }
+            float r[S];
+            const float4 *rec = reinterpret_cast<const float4 *>(w.rec + k * S);
+#pragma unroll
+            for (int q = 0; q < S / 4; ++q) {
+                const float4 v = rec[q];
+                r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+            }
             const float *cf = coef + 8 * b;
             const float isb2 = cf[4];
-            AdamK kmu{be, cf[0], isb2};
-            AdamK kch{be, cf[1], isb2};
-            AdamK kea{be, cf[2], isb2};
-            AdamK kew{be, cf[3], isb2};
-            AdamK kpi{be, cf[5], isb2};
+            const AdamK kmu{be, cf[0], isb2}, kch{be, cf[1], isb2}, kea{be, cf[2], isb2};
+            const AdamK kew{be, cf[3], isb2}, kpi{be, cf[5], isb2};
             float gmx = 0.f, gmy = 0.f;
-            if (rc.x <= rc.z) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
+            if (listed) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
+#pragma unroll
             for (int ch = 0; ch < C; ++ch) {
                 const int64_t x = kl * C + ch;
-                float pv = ea[x], mv = m_ea[x], vv = v_ea[x];
+                float pv = im.p.ea[x], mv = im.m.ea[x], vv = im.v.ea[x];
                 adam1(pv, s[5 + ch], mv, vv, kea);
-                ea[x] = pv; m_ea[x] = mv; v_ea[x] = vv;
-                if (g.linear) {
-                    if (rc.x <= rc.z) {
+                im.p.ea[x] = pv; im.m.ea[x] = mv; im.v.ea[x] = vv;
+                if (LIN) {
+                    if (listed) {
                         gmx -= r[7 + ch * E + 1] * s[5 + ch];
                         gmy -= r[7 + ch * E + 2] * s[5 + ch];
                     }
+#pragma unroll
                     for (int d = 0; d < 2; ++d) {
                         const int64_t xw = x * 2 + d;
-                        float pw = eW[xw], mw = m_eW[xw], vw = v_eW[xw];
+                        float pw = im.p.eW[xw], mw = im.m.eW[xw], vw = im.v.eW[xw];
                         adam1(pw, s[5 + (1 + d) * C + ch], mw, vw, kew);
-                        eW[xw] = pw; m_eW[xw] = mw; v_eW[xw] = vw;
+                        im.p.eW[xw] = pw; im.m.eW[xw] = mw; im.v.eW[xw] = vw;
                     }
                 }
             }
             const float gm[2] = {gmx * (float)im.W, gmy * (float)im.H};
+#pragma unroll
             for (int d = 0; d < 2; ++d) {
-                float pv = mu[2 * kl + d], mv = m_mu[2 * kl + d], vv = v_mu[2 * kl + d];
+                float pv = im.p.mu[2 * kl + d], mv = im.m.mu[2 * kl + d], vv = im.v.mu[2 * kl + d];
                 adam1(pv, gm[d], mv, vv, kmu);
-                mu[2 * kl + d] = pv; m_mu[2 * kl + d] = mv; v_mu[2 * kl + d] = vv;
+                im.p.mu[2 * kl + d] = pv; im.m.mu[2 * kl + d] = mv; im.v.mu[2 * kl + d] = vv;
             }
+#pragma unroll
             for (int d = 0; d < 3; ++d) {
-                float pv = chol[3 * kl + d], mv = m_chol[3 * kl + d], vv = v_chol[3 * kl + d];
+                float pv = im.p.chol[3 * kl + d], mv = im.m.chol[3 * kl + d];
+                float vv = im.v.chol[3 * kl + d];
                 adam1(pv, -s[d], mv, vv, kch);
-                chol[3 * kl + d] = pv; m_chol[3 * kl + d] = mv; v_chol[3 * kl + d] = vv;
+                im.p.chol[3 * kl + d] = pv; im.m.chol[3 * kl + d] = mv; im.v.chol[3 * kl + d] = vv;
             }
             if (im.p.logpi) {                              // gate weight: dL/dlogpi = S0
                 float pv = im.p.logpi[kl], mv = im.m.logpi[kl], vv = im.v.logpi[kl];
-                adam1(pv, s[5 + C * E], mv, vv, kpi);
+                adam1(pv, s[PI], mv, vv, kpi);
                 im.p.logpi[kl] = pv; im.m.logpi[kl] = mv; im.v.logpi[kl] = vv;
             }
-            if (!w.part)
-                for (int q = 0; q < g.GS; ++q) acc[q] = 0.0f;
+            if (!w.part && listed)     // an unlisted kernel's sums received nothing: still 0
+#pragma unroll
+                for (int q = 0; q < GS / 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     // Step counters advance once every CTA has read them.
@@ -221,7 +241,10 @@ cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, d
     const unsigned blocks = (unsigned)((g.K_total + 255) / 256);
     if (blocks == 0) return cudaSuccess;
     const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
-    k_fit_adam<<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    if (g.C == 1 && !g.linear) k_fit_adam<1, false><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else if (g.C == 1) k_fit_adam<1, true><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else if (!g.linear) k_fit_adam<3, false><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else k_fit_adam<3, true><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
     return cudaGetLastError();
 }
 

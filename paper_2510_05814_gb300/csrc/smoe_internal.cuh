@@ -71,10 +71,12 @@ struct Bufs {
 
 // Deterministic gradient sums of kernel k: the partial sums of the (tile, k)
 // pairs added in row-major tile order (the pair's position in a tile's
-// ascending list is found by binary search).
-__device__ __forceinline__ void gather_sums(const Geo &g, const Bufs &w, const ImgDev &im,
-                                            int64_t k, int4 rc, float *out) {
-    for (int q = 0; q < g.GS; ++q) out[q] = 0.0f;
+// ascending list is found by binary search).  GS sums, in registers.
+template <int GS>
+__device__ __forceinline__ void gather_sums(const Bufs &w, const ImgDev &im, int64_t k, int4 rc,
+                                            float (&out)[GS]) {
+#pragma unroll
+    for (int q = 0; q < GS; ++q) out[q] = 0.0f;
     for (int ty = rc.y; ty <= rc.w; ++ty)
         for (int tx = rc.x; tx <= rc.z; ++tx) {
             const int64_t t = im.t_off + (int64_t)ty * im.tiles_x + tx;
@@ -84,8 +86,9 @@ __device__ __forceinline__ void gather_sums(const Geo &g, const Bufs &w, const I
                 if (w.pair_k[mid] < k) lo = mid + 1; else hi = mid;
             }
             if (lo >= w.tile_off[t + 1] || w.pair_k[lo] != k) continue;
-            const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)lo * g.GS);
-            for (int q = 0; q < g.GS / 4; ++q) {
+            const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)lo * GS);
+#pragma unroll
+            for (int q = 0; q < GS / 4; ++q) {
                 const float4 v = src[q];
                 out[4 * q] += v.x; out[4 * q + 1] += v.y; out[4 * q + 2] += v.z; out[4 * q + 3] += v.w;
             }
