@@ -209,6 +209,18 @@ def test_mid_length_lists_are_bitexact(K):
     check_y(y.cpu().numpy(), ref, absm, "y")
 
 
+@pytest.mark.parametrize("W", [2048, 6000])
+def test_bin_bitexact_many_tiles(W):
+    """Wide kernels on large rasters (16384 and 140625 tiles, several prefix-
+    sum blocks): the lists are still bit-exact."""
+    p = rand_case(60, W, W, 1, 80, False, sig=(30.0, 200.0))
+    _, r = gpu_raster(p, W, W, 1, 16, 1.0)
+    off, pk = r.lists()
+    ref_off, ref_pk = om.bin_tiles(oracle_model(p, W, W, 1, 16))
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+
+
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_count_inrange_matches_oracle(tile):
     """The in-range pair count equals the number of (pixel, kernel) pairs
