@@ -109,6 +109,20 @@ class FitBatch:
     def params_of(self, b):
         return self.params[b]
 
+    def set_target(self, b, target):
+        """Point image b at another target tensor of the same shape (for
+        example the other half of a double buffer that a copy stream fills).
+        A single-image batch only rewrites the host-side struct; a batch of
+        several images re-uploads its image table (smoe_fit_init, which
+        synchronises)."""
+        t = self.targets[b]
+        assert target.shape == t.shape and target.dtype == t.dtype and target.is_contiguous()
+        self.targets[b] = target
+        if self.B == 1:
+            self._imgs[b].target = _ptr(target)
+        else:
+            self._setup(reset=False)
+
     def launch(self, n_iters=1, stream=None):
         """Enqueue n_iters iterations (no host synchronisation)."""
         check(_lib.load().smoe_fit(ctypes.byref(self._batch), self._imgs, self.pair_cap,
