@@ -12,19 +12,20 @@
 //
 // Forward (pixel-major): a warp owns a band of 64 pixels (2 adjacent pixels
 // per lane, 64/T rows) and walks the chunk, skipping every kernel whose mask
-// misses the band's rows; D = sum e and N_c = sum e m_c stay in FP32
+// misses the band's rows (ballot compaction), four kernels in flight on two
+// pairs of accumulators; D = sum e and N_c = sum e m_c stay in FP32
 // registers.  Pixel pairs use packed f32x2 arithmetic (IEEE per lane, the
 // same single rounding as the scalar predicate, so the inclusion decision is
 // bit-identical).  T = 8 has one band: its warps split the chunk and meet in
 // shared memory.
 //
-// Backward (item-major): every (row, kernel) pair of the chunk with its mask
-// bit set is one item; the CTA's threads take items in row-major order (so a
-// warp's lanes read the same row of pixel state, a broadcast, and add into
-// different kernels' sums).  An item walks the row's T pixels (packed pairs),
-// recomputes the gate and accumulates the raw moments below, adds them to the
-// kernel's sums in shared memory, and after the chunk one float4 atomic per 4
-// sums per (tile, kernel) goes to the global accumulator.
+// Backward (row-synchronous, lane = kernel): the chunk's kernels are grouped
+// 32 at a time by the centre of their row span; a warp walks the union of its
+// group's row masks, every lane evaluating its own kernel on the row's pixel
+// pairs against the pixel state read by broadcast from shared memory, and
+// keeps its kernel's raw sums (below) in registers until one float4 atomic
+// per 4 sums per (tile, kernel).  With float atomics the last round's groups
+// are shared by all warps row-interleaved, so no warp idles.
 //
 // Raw per-kernel sums (e = pi exp(-q/2); s = g sum_c G_c (m_c - y_c), g = e / D,
 // H_c = G_c / D, so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c;
@@ -92,7 +93,7 @@ struct Smem {
     uint32_t mask[G::NCH];
     int32_t kid[G::NCH];
     uint8_t flist[kNW][G::NCH];          // per-warp compacted kernel list of a band
-    uint8_t order[G::NCH];               // backward: kernels grouped by first row
+    uint8_t order[G::NCH];               // backward: kernels grouped by row-span centre
     int bcnt[2 * T], boff[2 * T];        // backward grouping buckets (2T - 1 keys)
     double lsum[kNW];
     long long next;                      // persistent launch: the CTA's next tile
@@ -208,7 +209,7 @@ __device__ __forceinline__ void fwd_pair(const float *r, float y0, float2 x2, fl
 // Accumulate D and N_c of one lane's two pixels (row `row`, columns col,
 // col+1 of the tile) over the staged kernels j = j0, j0 + step, ... whose
 // mask meets `band_mask`: the warp first compacts those kernels (ballot),
-// then evaluates them two at a time with independent accumulators.
+// then evaluates them four at a time on two pairs of accumulators.
 template <int C, bool LIN, int T>
 __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
                                          Smem<C, LIN, T> &sm, int nc, int j0, int step,
@@ -446,8 +447,9 @@ struct BwdAcc {
 // Backward over the tile's list; the pixel state is in sm.pst.  `staged`:
 // the first chunk is still in shared memory from the forward.  Each lane
 // owns one kernel of the chunk (kernels with an empty row mask are dropped;
-// the rest are grouped by their first row so that a warp's 32 kernels cover
-// similar rows) and the warp walks the union of its kernels' rows together:
+// the rest are grouped by the centre of their row span so that a warp's 32
+// kernels cover similar rows) and the warp walks the union of its kernels'
+// rows together:
 // every read of pixel state is a broadcast, lanes whose kernel misses the
 // row contribute zero, and each kernel's sums stay in its lane's registers
 // until one float4 atomic per 4 sums at the end.
