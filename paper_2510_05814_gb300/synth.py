@@ -267,9 +267,12 @@ def denoise_case(W=768, H=512, noise_var=0.01, seed=5):
 
 
 def ragged_sizes(n=64, seed=4):
-    """Log-uniform image sizes from 128x96 to 1920x1080 (both end points hit)."""
+    """Log-uniform image sizes from 128x96 to 1920x1080: t ~ U(0, 1) with the
+    first two draws set to the end points, W = round(128 * 15^t),
+    H = round(96 * 11.25^t)."""
     rng = np.random.default_rng(seed)
     t = rng.uniform(0.0, 1.0, n)
+    t[:2] = (0.0, 1.0)[:n]
     W = np.rint(128 * 15.0 ** t).astype(int)
     H = np.rint(96 * 11.25 ** t).astype(int)
     return list(zip(W.tolist(), H.tolist()))

@@ -142,3 +142,34 @@ def test_autograd_64_parameters_vs_oracle_and_central_differences(wl):
                 assert abs(got - fd) <= 1e-3 * max(abs(fd), 1e-2 * terms) + 1e-9, (k, gi, e, got, fd)
                 checked_fd += 1
     assert checked_fd >= 12
+
+
+def test_ragged_batch_fullsize_losses():
+    """Config 4 at full size: the 64 ragged images (128x96 .. 1920x1080,
+    K = pixels/16, 35 M pixels) as one fit batch.  After one fused iteration
+    the per-image MSE of the initial models, computed inside the batched tile
+    kernel, matches the oracle's dense FP64 render for the six smallest images
+    (whose tiles sit between the big images' in the ragged table) and is
+    finite for all."""
+    from paper_2510_05814_gb300.fit import FitBatch
+    sizes = synth.ragged_sizes(64, 4)
+    targets, params, nps = [], [], []
+    for i, (W, H) in enumerate(sizes):
+        t = synth.polygon_image(W, H, 3, 40, 400 + i, texture_amp=0.1)
+        p = synth.init_params(t, (W * H) // 16, 5.0, True, 400 + i)
+        targets.append(t)
+        nps.append(p)
+        params.append(api.SMoEParams.from_numpy(p))
+    fb = FitBatch([torch.tensor(t, device="cuda") for t in targets], params, 1,
+                  lr=synth.PAPER_LR, tile=T)
+    fb.run(1)
+    loss = fb.losses()[:, 0]
+    assert np.all(np.isfinite(loss)) and np.all(loss > 0)
+    small = sorted(range(64), key=lambda b: sizes[b][0] * sizes[b][1])[:6]
+    for b in small:
+        W, H = sizes[b]
+        p = nps[b]
+        m = om.Model(W, H, 3, p.mu, p.chol, p.ea, p.eW, tile=T)
+        y, _ = om.render(m)
+        ref = float(np.mean((y - targets[b].astype(np.float64)) ** 2))
+        assert loss[b] == pytest.approx(ref, rel=1e-5), (b, loss[b], ref)
