@@ -726,7 +726,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 8,
                     "copies": "pinned host target -> device each step on a copy stream "
-                              "(double buffer, overlapping the previous step); loss -> host"},
+                              "(double buffer, overlapping the previous step); loss -> host",
+                    "l2": "not flushed: steps back to back, as a caller runs them"},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clocks,
         }
