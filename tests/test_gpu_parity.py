@@ -190,6 +190,56 @@ def test_long_lists_use_bitmap_path():
         check_grad(a, b, name, t, rtol=1e-3)
 
 
+def test_bin_bitexact_many_seeds():
+    """Binning against the oracle on 120 random models (ragged rasters,
+    T in {8, 16, 32}, centres inside and outside the raster, thin and wide
+    anisotropic kernels): the lists are bit-exact every time."""
+    rng = np.random.default_rng(2024)
+    for seed in range(120):
+        T = (8, 16, 32)[seed % 3]
+        W, H = int(rng.integers(1, 97)), int(rng.integers(1, 97))
+        K = int(rng.integers(1, 60))
+        sig = (0.3, 3.0) if seed % 2 else (2.0, 25.0)
+        p = rand_case(5000 + seed, W, H, 1, K, False, sig=sig, span=(-0.2, 1.2))
+        _, r = gpu_raster(p, W, H, 1, T, 1.0)
+        off, pk = r.lists()
+        ref_off, ref_pk = om.bin_tiles(oracle_model(p, W, H, 1, T))
+        np.testing.assert_array_equal(off.astype(np.int64), ref_off, err_msg=f"seed {seed}")
+        np.testing.assert_array_equal(pk, ref_pk, err_msg=f"seed {seed}")
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_kernels_on_tile_edges(tile):
+    """Centres exactly on tile boundaries and corners, and boxes whose edge
+    falls on a boundary (radius a multiple of the tile): lists bit-exact,
+    render and gradients within the bars."""
+    W = H = 4 * tile
+    cs = np.array([[x, y] for x in (0, tile, 2 * tile, W) for y in (0, tile, 3 * tile)],
+                  np.float64)
+    K = len(cs)
+    rng = np.random.default_rng(tile)
+    r_px = tile * rng.integers(1, 3, K)                     # box half sides on the grid
+    a = np.sqrt(9.0) / r_px                                  # isotropic: r = 3 / a
+    chol = np.stack([a, np.zeros(K), a], 1).astype(np.float32)
+    p = synth.Params((cs / [W, H]).astype(np.float32), chol,
+                     rng.uniform(0, 1, (K, 3)).astype(np.float32),
+                     rng.normal(0, 0.05, (K, 3, 2)).astype(np.float32))
+    params, r = gpu_raster(p, W, H, 3, tile, 1.0)
+    off, pk = r.lists()
+    m = oracle_model(p, W, H, 3, tile)
+    ref_off, ref_pk = om.bin_tiles(m)
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    y, invd = r.render()
+    ref, _, absm = om.render(m, with_scale=True)
+    check_y(y.cpu().numpy(), ref, absm, "y")
+    gy = rng.normal(0, 1, (3, H, W))
+    g = r.backward(params, y, invd, gy=torch.tensor(gy, dtype=torch.float32, device="cuda"))
+    ref_g, terms = om.backward(m, gy=gy.astype(np.float32).astype(np.float64), with_scale=True)
+    for name, a_, b_, t_ in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref_g, terms):
+        check_grad(a_, b_, name, t_)
+
+
 @pytest.mark.parametrize("K", [400, 700, 1500])
 def test_mid_length_lists_are_bitexact(K):
     """Lists of 257-512 and 513-1024 ids take the warp register sorts with

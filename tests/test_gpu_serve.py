@@ -74,3 +74,22 @@ def test_budget_limits_concurrent_fits():
             live -= 1
         peak = max(peak, live)
     assert peak == 1
+
+
+def test_failed_fit_surfaces_as_an_error(monkeypatch):
+    """A host-side injected failure: the batch reports a CUDA error status
+    after a chunk; the server stops with an error instead of returning
+    results built on a failed fit."""
+    from paper_2510_05814_gb300 import fit as fit_mod
+    reqs = [r for r in requests() if isinstance(r, FitRequest)][:2]
+    calls = {"n": 0}
+    real = fit_mod.FitBatch.status_code
+
+    def failing(self):
+        calls["n"] += 1
+        return 3 if calls["n"] == 1 else real(self)          # SMOE_ERR_CUDA once
+
+    monkeypatch.setattr(fit_mod.FitBatch, "status_code", failing)
+    srv = serve.Server(8 << 30, chunk=10)
+    with pytest.raises(RuntimeError, match="fit status 3"):
+        srv.run(reqs, realtime=False)
