@@ -68,7 +68,9 @@ typedef enum {
     SMOE_ERR_ARG = 1,        /* bad argument (sizes, NULL, alignment) */
     SMOE_ERR_CAPACITY = 2,   /* pair count above pair_cap (device status) */
     SMOE_ERR_CUDA = 3,       /* a CUDA call or launch failed */
-    SMOE_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up */
+    SMOE_ERR_TIMEOUT = 4,    /* reserved: no kernel of this library waits on another
+                                (the persistent launch takes tiles from an atomic
+                                counter), so none returns it */
     SMOE_ERR_WORKSPACE = 5   /* workspace too small or misaligned */
 } smoe_status;
 
@@ -135,12 +137,15 @@ SMOE_API smoe_status smoe_render(const smoe_desc *d, int64_t K, const void *ws, 
                         float *y, float *inv_d, const int32_t *status, void *stream);
 
 /* Backward of smoe_render (the gradient-descent fit through the rasteriser,
- * Sec. III-D): gradients of a loss L w.r.t. mu, chol, ea, eW, ADDED into
- * `grad` (caller zeroes it).  Upstream: gy = dL/dy (C x H x W) or, if gy is
- * NULL, the MSE sum((y - target)^2) / (C H W) against `target`.  Gates are
- * recomputed from the lists; y and inv_d are the outputs of smoe_render.
- * Per-kernel partial sums are accumulated with atomics in `ws`, so the result
- * is deterministic only up to FP32 summation order. */
+ * Sec. III-D): gradients of a loss L w.r.t. mu, chol, ea, eW and, when
+ * grad->logpi is set, the gate weights logpi (Eq. 4; at pi = 1 when p->logpi
+ * is NULL), ADDED into `grad` (caller zeroes it).  Upstream: gy = dL/dy
+ * (C x H x W) or, if gy is NULL, the MSE sum((y - target)^2) / (C H W)
+ * against `target`.  Gates are recomputed from the lists; y and inv_d are the
+ * outputs of smoe_render with the same desc (d->gate = 1: the RBF sum of
+ * Eq. 1, whose gradient has no -y term).  Per-kernel partial sums are
+ * accumulated with atomics in `ws`, so the result is deterministic only up to
+ * FP32 summation order. */
 SMOE_API smoe_status smoe_render_backward(const smoe_desc *d, const smoe_params *p, void *ws,
                                  size_t ws_bytes, const int32_t *tile_off,
                                  const int32_t *pair_k, const float *y, const float *inv_d,

@@ -455,7 +455,6 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-int64_t scan_blocks(int64_t n_tiles) { return (n_tiles + kScanChunk - 1) / kScanChunk; }
 
 cudaError_t launch_exscan(int64_t n, const int32_t *cnt, long long *bsum, int32_t *off,
                           int64_t *total, int32_t *n_long, int32_t *cursor, int64_t cap,

@@ -160,11 +160,10 @@ cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
                           cudaStream_t st);
 // Exclusive prefix sum of n counters into off[0..n] (off[n] = min(total, cap),
 // *total = the sum, cursor[0..n) zeroed; a total above cap sets
-// SMOE_ERR_CAPACITY); needs scan_blocks(n) entries of bsum.
+// SMOE_ERR_CAPACITY); needs ceil(n / 4096) entries of bsum.
 cudaError_t launch_exscan(int64_t n, const int32_t *cnt, long long *bsum, int32_t *off,
                           int64_t *total, int32_t *n_long, int32_t *cursor, int64_t cap,
                           int32_t *status, cudaStream_t st);
-int64_t scan_blocks(int64_t n_tiles);
 // Scratch of smoe_render_points: per-tile counts / cursors / offsets of the
 // points, prefix-sum block sums, each point's tile and the tile-sorted order.
 struct PointBufs {
