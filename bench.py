@@ -167,6 +167,20 @@ def oracle_sample(wl, size):
     return pairs, time.perf_counter() - t0, om.threads(), int(p.mu.shape[0])
 
 
+def binned_sample(wl, size):
+    """Time the binned CPU baseline (oracle binning + per-tile list walks,
+    FP64, OpenMP) on a crop: one step's binning, forward, MSE and backward;
+    returns (pairs in the metric's count, seconds, threads, kernels)."""
+    import oracle as om
+    t, p = crop_workload(wl, size)
+    m = om.Model(size, size, t.shape[0], p.mu, p.chol, p.ea, p.eW, tile=wl.tile, qmax=wl.qmax)
+    t0 = time.perf_counter()
+    off, pk = om.bin_tiles(m)
+    om.fwd_bwd_binned(m, t, lists=(off, pk))
+    sec = time.perf_counter() - t0
+    return evaluated_pairs(off, size, size, wl.tile), sec, om.threads(), int(p.mu.shape[0])
+
+
 def dist_init(backend="nccl"):
     """Rank layout from the torchrun environment; joins the process group
     when WORLD_SIZE > 1 (NCCL on GPUs; gloo for the CPU tests of this logic)."""
@@ -491,6 +505,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-crop", type=int, default=512)
     ap.add_argument("--ref-crop", type=int, default=256)
+    ap.add_argument("--binned-crop", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--mode", default="fit",
                     choices=["fit", "batched", "serve", "denoise", "quality"],
@@ -678,12 +693,18 @@ def main():
         ncu = NCU
     traffic = ncu["bytes_per_launch"] if ncu else None
 
-    cpu = None
+    cpu = cpu_binned = None
     if rank == 0 and world == 1 and not args.no_cpu:
         pairs_c, s_c, thr, kc = oracle_sample(wl, args.cpu_crop)
         cpu = {"value": pairs_c / s_c / 1e9, "unit": UNIT, "cores": thr, "kind": "oracle",
                "sample": f"{args.cpu_crop}x{args.cpu_crop} centre crop of the workload with its "
                          f"{kc} kernels; one dense forward + MSE backward ({s_c:.1f} s)"}
+        pairs_b, s_b, thr_b, kb = binned_sample(wl, args.binned_crop)
+        cpu_binned = {"value": pairs_b / s_b / 1e9, "unit": UNIT, "cores": thr_b,
+                      "kind": "binned oracle (CPU baseline, labelled)",
+                      "sample": f"{args.binned_crop}x{args.binned_crop} centre crop with its {kb} "
+                                f"kernels; binning + per-tile forward, MSE, backward in FP64 "
+                                f"({s_b:.1f} s)"}
 
     if rank == 0:
         out = {
@@ -723,6 +744,7 @@ def main():
                                     "Gpoints_per_s": pts.shape[0] / pts_ms / 1e6,
                                     "raster": "jittered 10x raster over a 205x205 crop"},
             "cpu_baseline": cpu,
+            "cpu_baseline_binned": cpu_binned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
                     "d2h_bytes_per_step": 8,
                     "copies": "pinned host target -> device each step on a copy stream "

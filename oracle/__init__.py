@@ -77,6 +77,8 @@ def _load():
         lib.om_fit.argtypes = [MP, P, ctypes.c_int32, P, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, P, P, P, P, P, P]
         lib.om_fit.restype = None
+        lib.om_fwd_bwd_binned.argtypes = [MP, P, P, P, P, P, P, P]
+        lib.om_fwd_bwd_binned.restype = ctypes.c_double
         lib.om_threads.argtypes = []
         lib.om_threads.restype = ctypes.c_int32
         _lib = lib
@@ -269,6 +271,24 @@ def backward(m: Model, gy=None, target=None, kernels=None, with_scale=False):
                     _ptr(sc[4]))
     k = 5 if m.logpi is not None else 4
     return (tuple(g[:k]), tuple(sc[:k])) if with_scale else tuple(g[:k])
+
+
+def fwd_bwd_binned(m: Model, target, lists=None):
+    """The binned CPU baseline: forward, MSE and backward with each pixel
+    visiting only its tile's list (om_bin's lists, computed here unless
+    given).  Returns (mse, (g_mu, g_chol, g_ea, g_eW)); equals the dense
+    render + backward up to the order of the FP64 sums."""
+    lib = _load()
+    c = m._c()
+    off, pk = lists if lists is not None else bin_tiles(m)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    pk = np.ascontiguousarray(pk, dtype=np.int32)
+    t_ = np.ascontiguousarray(target, dtype=np.float32)
+    g = [np.zeros((m.K, 2)), np.zeros((m.K, 3)), np.zeros((m.K, m.C)),
+         np.zeros((m.K, m.C, 2)) if m.linear else None]
+    mse = lib.om_fwd_bwd_binned(ctypes.byref(c), _ptr(t_), _ptr(off), _ptr(pk),
+                                *[_ptr(x) for x in g])
+    return float(mse), tuple(g)
 
 
 def adam(p, g, m_, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):

@@ -542,6 +542,122 @@ void om_fit(om_model *m, const float *target, int32_t n_it, const double lr[6],
     free(y);
 }
 
+/* The same forward, MSE and backward as om_render + om_backward(target), but
+ * each pixel visits only its tile's list (tile_off / pair_k from om_bin over
+ * all tiles): the binned CPU baseline.  The lists are conservative, so the
+ * result equals the dense one up to the order of the FP64 sums.  Gradients
+ * (API units, arrays of K rows, eW may be NULL for constant experts) are
+ * overwritten; returns the MSE.  OpenMP over tiles, per-thread gradient
+ * buffers added at the end. */
+double om_fwd_bwd_binned(const om_model *m, const float *target, const int64_t *tile_off,
+                         const int32_t *pair_k, double *g_mu, double *g_chol, double *g_ea,
+                         double *g_eW)
+{
+    const int C = m->C;
+    const int32_t T = m->T, tiles_x = (m->W + T - 1) / T, tiles_y = (m->H + T - 1) / T;
+    const int64_t n_tiles = (int64_t)tiles_x * tiles_y, HW = (int64_t)m->W * m->H;
+    const int64_t K = m->K, G = 2 + 3 + C + 2 * C;     /* per-kernel gradient row */
+    const double norm = 2.0 / ((double)C * (double)HW);
+    double se = 0.0;
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    double *buf = (double *)calloc((size_t)nth * (size_t)(K * G), sizeof(double));
+#pragma omp parallel reduction(+ : se)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *gb = buf + (int64_t)tid * K * G;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            const int32_t x0 = (int32_t)(t % tiles_x) * T, y0 = (int32_t)(t / tiles_x) * T;
+            for (int32_t j = y0; j < y0 + T && j < m->H; ++j)
+                for (int32_t i = x0; i < x0 + T && i < m->W; ++i) {
+                    const int64_t px = (int64_t)j * m->W + i;
+                    double D = 0.0, N[3] = {0.0, 0.0, 0.0};
+                    for (int64_t q = tile_off[t]; q < tile_off[t + 1]; ++q) {
+                        const int64_t k = pair_k[q];
+                        if (!om_included(m, k, i, j)) continue;
+                        om_pair pr;
+                        pair_value(m, k, i, j, &pr);
+                        D += pr.e;
+                        for (int ch = 0; ch < C; ++ch) N[ch] += pr.e * pr.mexp[ch];
+                    }
+                    if (!(D > 0.0)) {
+                        for (int ch = 0; ch < C; ++ch) {
+                            const double d = -(double)target[ch * HW + px];
+                            se += d * d;
+                        }
+                        continue;
+                    }
+                    double Y[3], Gp[3];
+                    const double nrm = m->rbf ? 1.0 : D;
+                    for (int ch = 0; ch < C; ++ch) {
+                        Y[ch] = N[ch] / nrm;
+                        const double d = Y[ch] - (double)target[ch * HW + px];
+                        se += d * d;
+                        Gp[ch] = norm * d;
+                    }
+                    for (int64_t q = tile_off[t]; q < tile_off[t + 1]; ++q) {
+                        const int64_t k = pair_k[q];
+                        if (!om_included(m, k, i, j)) continue;
+                        om_pair pr;
+                        pair_value(m, k, i, j, &pr);
+                        float mx, my, a, b, c;
+                        kernel_px(m, k, &mx, &my, &a, &b, &c);
+                        const double g = m->rbf ? pr.e : pr.e / D;
+                        double r = 0.0;
+                        for (int ch = 0; ch < C; ++ch)
+                            r += Gp[ch] * (pr.mexp[ch] - (m->rbf ? 0.0 : Y[ch]));
+                        const double sv = g * r;
+                        double *row = gb + k * G;
+                        row[0] += sv * pr.z0 * (double)a;                       /* mu_px x */
+                        row[1] += sv * (pr.z0 * (double)b + pr.z1 * (double)c); /* mu_px y */
+                        row[2] += -sv * pr.z0 * pr.dx;
+                        row[3] += -sv * pr.z0 * pr.dy;
+                        row[4] += -sv * pr.z1 * pr.dy;
+                        for (int ch = 0; ch < C; ++ch) {
+                            const double gG = g * Gp[ch];
+                            row[5 + ch] += gG;
+                            if (m->linear) {
+                                float w0 = m->eW[(k * C + ch) * 2], w1 = m->eW[(k * C + ch) * 2 + 1];
+                                if (m->scale != 1.0f) { w0 = w0 / m->scale; w1 = w1 / m->scale; }
+                                row[0] -= gG * (double)w0;
+                                row[1] -= gG * (double)w1;
+                                row[5 + C + 2 * ch] += gG * pr.dx;
+                                row[5 + C + 2 * ch + 1] += gG * pr.dy;
+                            }
+                        }
+                    }
+                }
+        }
+    }
+    const double inv_s = 1.0 / (double)m->scale;
+    for (int64_t k = 0; k < K; ++k) {
+        double row[2 + 3 + 3 + 6];
+        for (int64_t x = 0; x < G; ++x) {
+            double v = 0.0;
+            for (int th = 0; th < nth; ++th) v += buf[((int64_t)th * K + k) * G + x];
+            row[x] = v;
+        }
+        g_mu[2 * k] = row[0] * (double)m->W;
+        g_mu[2 * k + 1] = row[1] * (double)m->H;
+        for (int d = 0; d < 3; ++d) g_chol[3 * k + d] = row[2 + d] * inv_s;
+        for (int ch = 0; ch < C; ++ch) {
+            g_ea[k * C + ch] = row[5 + ch];
+            if (m->linear && g_eW) {
+                g_eW[(k * C + ch) * 2] = row[5 + C + 2 * ch] * inv_s;
+                g_eW[(k * C + ch) * 2 + 1] = row[5 + C + 2 * ch + 1] * inv_s;
+            }
+        }
+    }
+    free(buf);
+    return se / (double)(HW * C);
+}
+
 /* Number of OpenMP threads the oracle uses. */
 int32_t om_threads(void)
 {

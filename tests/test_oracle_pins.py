@@ -879,3 +879,21 @@ def test_render_term_scale_bounds_the_render(om):
     y2, _, s2 = om.render(m2, with_scale=True)
     cov = s2 > 0
     assert np.any(s2[cov] > np.abs(y2[cov]) * (1 + 1e-9))   # cancelling pixels
+
+
+def test_binned_baseline_equals_dense(om):
+    """The binned CPU baseline (per-tile lists) gives the dense oracle's MSE
+    and gradients: the lists are conservative, only the FP64 summation order
+    differs."""
+    rng = np.random.default_rng(95)
+    for linear, tile, rbf in ((True, 8, False), (False, 16, False), (True, 16, True)):
+        m = rand_model(om, rng, W=37, H=29, K=14, linear=linear, tile=tile)
+        m.rbf = rbf
+        t = rng.uniform(0, 1, (3, 29, 37)).astype(np.float32)
+        mse, g = om.fwd_bwd_binned(m, t)
+        y, _ = om.render(m)
+        assert mse == pytest.approx(float(np.mean((y - t) ** 2)), rel=1e-12)
+        ref = om.backward(m, target=t)
+        for a, b in zip(g, ref):
+            if b is not None:
+                np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-14 * np.abs(b).max())
