@@ -461,14 +461,15 @@ def run_quality(args):
 
 def run_serve(args):
     """Poisson arrivals (50 req/s): fit requests (ragged sizes, half of them
-    denoising with N(0, 0.05) noise, `iters` Adam steps) and render requests
-    (a fitted model at 1-4x); continuous batching vs one request at a time."""
+    denoising with N(0, 0.05) noise as MM-RSMoE with --mm-models models,
+    `iters` Adam steps) and render requests (a fitted model at 1-4x);
+    continuous batching vs one request at a time."""
     import numpy as np
     import torch
     from paper_2510_05814_gb300 import build, serve
     build.build()
     reqs = serve.poisson_workload(args.fits, args.renders, args.rate, iters=args.iters,
-                                  sizes=None)
+                                  sizes=None, mm_models=args.mm_models)
     srv = serve.Server(args.budget_gb * (1 << 30), chunk=25)
     t0 = time.perf_counter()
     res_b = srv.run(reqs, realtime=True)
@@ -484,6 +485,7 @@ def run_serve(args):
     print(json.dumps({
         "metric": "serving: fit/render request latency p50/p99 and throughput, continuous "
                   "batching vs one request at a time", "mode": "serve",
+        "mm_models_per_denoising_request": args.mm_models,
         "requests": len(reqs), "fits": len(fits), "rate_per_s": args.rate, "iters": args.iters,
         "batched": {"wall_s": t_b, "req_per_s": len(reqs) / t_b,
                     "all": serve.latency_stats(res_b), "fit": serve.latency_stats(split(res_b, "fit")),
@@ -520,6 +522,8 @@ def main():
     ap.add_argument("--renders", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--mm-models", type=int, default=4,
+                    help="serve: MM-RSMoE models per denoising request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

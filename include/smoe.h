@@ -262,6 +262,27 @@ SMOE_API smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smo
                                           int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
                                           int32_t *status, void *stream);
 
+/* Multi-model fusion (Sec. V-C, Eq. 11) of H separate models on any raster:
+ * y = (1/H) sum_h y_h, each y_h the render of models[h] on d's W x H raster
+ * at d->scale (so a denoised MM-RSMoE result can be resampled at 1-4x), in
+ * one binning pass over the H models and one averaging launch; y_h is what
+ * smoe_render gives for model h, and H = 1 returns that render bit for bit.
+ *   models: H parameter sets (device SoA; logpi all set or all NULL)
+ *   ws: smoe_render_mean_workspace_size(d, models, H, pair_cap) bytes
+ *       (256-byte aligned); pair_cap bounds the (tile, kernel) pairs of all
+ *       H models together
+ *   y: out, C x H x W (d's raster); status: device word, zeroed by the
+ *      caller; a pair count above pair_cap sets SMOE_ERR_CAPACITY and y is
+ *      then not written
+ * With H > 1 the call uploads the H models' table into ws and synchronises
+ * the stream first (not capturable in a graph). */
+SMOE_API smoe_status smoe_render_mean_workspace_size(const smoe_desc *d,
+                                                     const smoe_params *models, int32_t H,
+                                                     int64_t pair_cap, size_t *bytes);
+SMOE_API smoe_status smoe_render_mean(const smoe_desc *d, const smoe_params *models, int32_t H,
+                                      void *ws, size_t ws_bytes, int64_t pair_cap, float *y,
+                                      int32_t *status, void *stream);
+
 /* Native sharpening by kernel editing (Sec. II-B, Sec. VII-C): the kernel
  * bandwidths divided by a sharpening factor f, i.e. L' = f L (P' = f^2 P):
  * chol_out[i] = f * chol_in[i] for the 3K entries, each rounded to float

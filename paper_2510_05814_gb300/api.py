@@ -293,6 +293,38 @@ def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0, sharpen_facto
     return y, inv_d, r
 
 
+def render_mean(models, W, H, tile=16, qmax=9.0, scale=1.0, rbf=False, pair_cap=None,
+                stream=None):
+    """Multi-model fusion (Sec. V-C, Eq. 11) of separate models (a list of
+    SMoEParams) on a W x H raster at `scale`: the per-pixel mean of their
+    renders, one binning pass and one averaging launch.  Returns (C, H, W)."""
+    lib = _lib.load()
+    Hm = len(models)
+    d = RasterDesc(W, H, models[0].C, tile, models[0].linear, qmax, scale, rbf).c()
+    arr = (_lib.Params * Hm)(*[m.c() for m in models])
+    K = sum(m.K for m in models)
+    cap = int(pair_cap if pair_cap is not None else 12 * K * max(1.0, scale * scale) + 4096)
+    y = torch.empty(models[0].C, H, W, dtype=torch.float32, device=models[0].mu.device)
+    status = torch.zeros(1, dtype=torch.int32, device=y.device)
+    while True:
+        n = ctypes.c_size_t(0)
+        check(lib.smoe_render_mean_workspace_size(ctypes.byref(d), arr, Hm, cap, ctypes.byref(n)),
+              "smoe_render_mean_workspace_size")
+        raw = torch.empty(n.value + 256, dtype=torch.uint8, device=y.device)
+        off = (-raw.data_ptr()) % 256
+        ws = raw[off:off + n.value]
+        status.zero_()
+        check(lib.smoe_render_mean(ctypes.byref(d), arr, Hm, _ptr(ws), ws.numel(), cap, _ptr(y),
+                                   _ptr(status), _stream(stream)), "smoe_render_mean")
+        st = smoe_get_status(status, stream)
+        if st == _lib.SMOE_ERR_CAPACITY:
+            cap = 2 * cap
+            continue
+        if st != _lib.SMOE_OK:
+            raise SmoeError(st, "smoe_render_mean")
+        return y
+
+
 def render_points(params: SMoEParams, W, H, xy, tile=16, qmax=9.0, sharpen_factor=None,
                   rbf=False):
     """Resample the model fitted on a W x H raster at the (n, 2) points

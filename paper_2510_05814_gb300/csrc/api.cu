@@ -507,6 +507,78 @@ smoe_status smoe_count_inrange(const smoe_desc *d, int64_t K, const void *ws, si
                                             static_cast<cudaStream_t>(stream)));
 }
 
+// H models rendered on one raster (d, including its scale), as a batch of H
+// images of that size: the binning and the averaging launch of Eq. 11.
+static bool mean_geo(const smoe_desc *d, const smoe_params *models, int32_t H, Geo *g,
+                     std::vector<ImgDev> *tab) {
+    if (!desc_ok(d) || !models || H <= 0) return false;
+    int64_t K_total = 0;
+    const int tx = (d->W + d->tile - 1) / d->tile, ty = (d->H + d->tile - 1) / d->tile;
+    tab->assign(H, ImgDev{});
+    for (int h = 0; h < H; ++h) {
+        if (!params_ok(&models[h], d)) return false;
+        if ((models[h].logpi != nullptr) != (models[0].logpi != nullptr)) return false;
+        ImgDev &im = (*tab)[h];
+        im.W = d->W;
+        im.H = d->H;
+        im.tiles_x = tx;
+        im.tiles_y = ty;
+        im.K = models[h].K;
+        im.k_off = K_total;
+        im.t_off = (int64_t)h * tx * ty;
+        im.p = models[h];
+        im.iters = 1;
+        K_total += models[h].K;
+    }
+    if (K_total > 0x7fffffffLL || (int64_t)H * tx * ty > kMaxTiles) return false;
+    *g = make_geo(d, K_total);
+    g->B = H;
+    g->tiles_total = (int64_t)H * tx * ty;
+    g->table = nullptr;
+    if (H == 1) g->one = (*tab)[0];
+    return true;
+}
+
+smoe_status smoe_render_mean_workspace_size(const smoe_desc *d, const smoe_params *models,
+                                            int32_t H, int64_t pair_cap, size_t *bytes) {
+    Geo g;
+    std::vector<ImgDev> tab;
+    if (!mean_geo(d, models, H, &g, &tab) || pair_cap < 0 || pair_cap > 0x7fffffffLL || !bytes)
+        return SMOE_ERR_ARG;
+    *bytes = layout(g.K_total, g.tiles_total, pair_cap, g.S, g.GS, g.B, true).total;
+    return SMOE_OK;
+}
+
+smoe_status smoe_render_mean(const smoe_desc *d, const smoe_params *models, int32_t H, void *ws,
+                             size_t ws_bytes, int64_t pair_cap, float *y, int32_t *status,
+                             void *stream) {
+    Geo g;
+    std::vector<ImgDev> tab;
+    if (!mean_geo(d, models, H, &g, &tab) || pair_cap < 0 || pair_cap > 0x7fffffffLL || !y ||
+        !status)
+        return SMOE_ERR_ARG;
+    const Layout L = layout(g.K_total, g.tiles_total, pair_cap, g.S, g.GS, g.B, true);
+    if (!ws_ok(ws, ws_bytes, L.total)) return SMOE_ERR_WORKSPACE;
+    char *b = static_cast<char *>(ws);
+    Bufs w = make_bufs(ws, L);
+    w.tile_off = reinterpret_cast<int32_t *>(b + L.tile_off);
+    w.pair_k = reinterpret_cast<int32_t *>(b + L.pair_k);
+    w.n_pairs = reinterpret_cast<int64_t *>(b + L.n_pairs);
+    w.pair_cap = pair_cap;
+    w.status = status;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (H > 1) {
+        g.table = reinterpret_cast<const ImgDev *>(b + L.table);
+        e = cudaMemcpyAsync(b + L.table, tab.data(), sizeof(ImgDev) * tab.size(),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host table is freed on return
+    }
+    if (e == cudaSuccess) e = launch_bin(g, w, st);
+    if (e == cudaSuccess) e = launch_render_mean(g, w, y, st);
+    return cuda_status(e);
+}
+
 smoe_status smoe_get_status(const int32_t *status, void *stream) {
     if (!status) return SMOE_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -15,6 +15,10 @@ continuous batching.
 - Render requests run on a second stream, so they overlap the fit chunks.
 - Fits run in the deterministic accumulation mode by default: an image's
   result is then bit-identical whatever else shares the batch.
+- A denoising request may ask for MM-RSMoE (Sec. V-C): its `models` models,
+  started from lattices shifted by the window offsets, are slots of the same
+  batch; the result is the per-pixel mean of their renders (Eq. 11), and a
+  later render request resamples that fused model at its scale.
 
 `serve_plain` runs the same requests one at a time, one image per launch,
 in arrival order: the baseline the batched server is compared with.
@@ -29,8 +33,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import synth
-from .api import Rasterizer, RasterDesc, SMoEParams
+from . import denoise, synth
+from .api import Rasterizer, RasterDesc, SMoEParams, render_mean
 from .fit import FitBatch
 
 
@@ -44,6 +48,7 @@ class FitRequest:
     denoise: bool = False              # the image carries noise (result = fitted render)
     arrival: float = 0.0
     seed: int = 0
+    models: int = 1                    # > 1: MM-RSMoE with that many models (Sec. V-C)
 
 
 @dataclass
@@ -93,6 +98,7 @@ class _Slot:
     nbytes: int = 0
     pairs: int = 0
     losses: list = field(default_factory=list)
+    member: int = 0                    # index of the model inside an MM-RSMoE request
 
 
 class Server:
@@ -113,18 +119,22 @@ class Server:
         self.events = []                 # (t, what) trace
 
     # -- slots
-    def _make_slot(self, r: FitRequest):
+    def _make_slots(self, r: FitRequest):
+        """One slot per model of the request (r.models > 1: the MM-RSMoE set,
+        lattices shifted by the window offsets; all share the target)."""
         C, H, W = r.image.shape
         K = max(1, (H * W) // r.pixels_per_kernel)
-        p0 = synth.init_params(r.image, K, r.sigma, True, r.seed)
+        slots = []
         with torch.cuda.stream(self.fit_stream):
             tgt = torch.tensor(r.image, device="cuda")
-            p = SMoEParams.from_numpy(p0)
-            s = _Slot(r, tgt, p, p.zeros_like(), p.zeros_like())
-            rr = Rasterizer(RasterDesc(W, H, C, self.tile, True, self.qmax), K).bin(p)
-            s.pairs = int(rr.n_pairs.item())
-        s.nbytes = fit_bytes(C, H, W, K)
-        return s
+            for h, p in enumerate(denoise.init_models(r.image, r.models, K, r.sigma, True,
+                                                      seed=r.seed)):
+                s = _Slot(r, tgt, p, p.zeros_like(), p.zeros_like(), member=h)
+                rr = Rasterizer(RasterDesc(W, H, C, self.tile, True, self.qmax), K).bin(p)
+                s.pairs = int(rr.n_pairs.item())
+                s.nbytes = fit_bytes(C, H, W, K)
+                slots.append(s)
+        return slots
 
     def _form_batch(self, slots, slack=1.5):
         cap = int(slack * sum(s.pairs for s in slots)) + 4096
@@ -152,20 +162,35 @@ class Server:
             ev.record()
         return ev
 
-    def _finish_fit(self, s: _Slot, b, now):
+    def _finish_fit(self, group, now):
+        """Result of a request whose slots (one, or its MM-RSMoE models in
+        member order) have all finished: the render, or the fused render."""
+        s = group[0]
         C, H, W = s.target.shape
         with torch.cuda.stream(self.fit_stream):
-            losses = np.asarray(s.losses)
-            r = Rasterizer(RasterDesc(W, H, C, self.tile, True, self.qmax), s.params.K).bin(s.params)
-            y, _ = r.render()
+            losses = np.mean([np.asarray(g.losses) for g in group], axis=0)
+            if len(group) == 1:
+                r = Rasterizer(RasterDesc(W, H, C, self.tile, True, self.qmax),
+                               s.params.K).bin(s.params)
+                y, _ = r.render()
+            else:
+                y = render_mean([g.params for g in group], W, H, self.tile, self.qmax)
             out = y.cpu().numpy()
         psnr = synth_psnr(out, s.req.image)
-        self.models[s.req.rid] = (s.params, (C, H, W))
+        self.models[s.req.rid] = ([g.params for g in group], (C, H, W))
         return Result(s.req.rid, "fit", s.req.arrival, now(), out, psnr, losses)
 
     def _start_render(self, q: RenderRequest):
-        params, (C, H, W) = self.models[q.model]
+        models, (C, H, W) = self.models[q.model]
         Ho, Wo = int(round(H * q.scale)), int(round(W * q.scale))
+        if len(models) > 1:                  # a fused MM-RSMoE model (synchronous)
+            with torch.cuda.stream(self.render_stream):
+                y = render_mean(models, Wo, Ho, self.tile, self.qmax, q.scale)
+                host = y.cpu()
+                ev = torch.cuda.Event()
+                ev.record()
+            return (q, None, host, ev)
+        params = models[0]
         with torch.cuda.stream(self.render_stream):
             r = Rasterizer(RasterDesc(Wo, Ho, C, self.tile, True, self.qmax, q.scale), params.K,
                            pair_cap=int(12 * params.K * max(1.0, q.scale * q.scale)))
@@ -196,13 +221,13 @@ class Server:
             while fits_q:
                 r = fits_q[0]
                 C, H, W = r.image.shape
-                need = fit_bytes(C, H, W, max(1, (H * W) // r.pixels_per_kernel))
+                need = r.models * fit_bytes(C, H, W, max(1, (H * W) // r.pixels_per_kernel))
                 if self.used + need > self.budget and (slots or inflight):
                     break
                 fits_q.popleft()
-                s = self._make_slot(r)
-                self.used += s.nbytes
-                slots.append(s)
+                for s in self._make_slots(r):
+                    self.used += s.nbytes
+                    slots.append(s)
                 changed = True
                 self.events.append((now(), f"admit fit {r.rid}"))
             # start renders whose model is resident
@@ -234,14 +259,16 @@ class Server:
                     continue
                 if st != 0:
                     raise RuntimeError(f"fit status {st}")
-                keep = []
-                for b, s in enumerate(slots):
+                keep, finished = [], collections.OrderedDict()
+                for s in slots:
                     if s.done >= s.req.iters:
-                        results.append(self._finish_fit(s, b, now))
+                        finished.setdefault(s.req.rid, []).append(s)
                         self.used -= s.nbytes
-                        self.events.append((now(), f"finish fit {s.req.rid}"))
                     else:
                         keep.append(s)
+                for rid, group in finished.items():
+                    results.append(self._finish_fit(sorted(group, key=lambda g: g.member), now))
+                    self.events.append((now(), f"finish fit {rid}"))
                 if len(keep) != len(slots):
                     slots = keep
                     self.batch = None
@@ -249,9 +276,10 @@ class Server:
             still = []
             for (q, r, host, ev) in inflight:
                 if ev.query():
-                    if int(r.status.item()) != 0:    # pair buffer too small: redo, growing it
+                    if r is not None and int(r.status.item()) != 0:
+                        # pair buffer too small: redo, growing it
                         with torch.cuda.stream(self.render_stream):
-                            r.bin(self.models[q.model][0])
+                            r.bin(self.models[q.model][0][0])
                             y, _ = r.render()
                             host = y.cpu()
                     results.append(Result(q.rid, "render", q.arrival, now(), host.numpy()))
@@ -281,29 +309,39 @@ def serve_plain(requests, tile=16, lr=synth.PAPER_LR, qmax=9.0, realtime=True, g
         if isinstance(r, FitRequest):
             C, H, W = r.image.shape
             K = max(1, (H * W) // r.pixels_per_kernel)
-            p = SMoEParams.from_numpy(synth.init_params(r.image, K, r.sigma, True, r.seed))
             tgt = torch.tensor(r.image, device="cuda")
-            fb = FitBatch([tgt], [p], r.iters, lr=lr, tile=tile, qmax=qmax,
-                          deterministic=deterministic)
-            if graphs:
-                fb.capture(r.iters)
-                fb.graph.replay()
+            ps, losses = [], []
+            for p in denoise.init_models(r.image, r.models, K, r.sigma, True, seed=r.seed):
+                fb = FitBatch([tgt], [p], r.iters, lr=lr, tile=tile, qmax=qmax,
+                              deterministic=deterministic)
+                if graphs:
+                    fb.capture(r.iters)
+                    fb.graph.replay()
+                else:
+                    fb.launch(r.iters)
+                st = fb.status_code()
+                if st != 0:
+                    raise RuntimeError(f"fit status {st}")
+                ps.append(p)
+                losses.append(fb.losses()[0])
+            if len(ps) == 1:
+                rr = Rasterizer(RasterDesc(W, H, C, tile, True, qmax), K).bin(ps[0])
+                y, _ = rr.render()
             else:
-                fb.launch(r.iters)
-            st = fb.status_code()
-            if st != 0:
-                raise RuntimeError(f"fit status {st}")
-            rr = Rasterizer(RasterDesc(W, H, C, tile, True, qmax), K).bin(p)
-            y, _ = rr.render()
+                y = render_mean(ps, W, H, tile, qmax)
             out = y.cpu().numpy()
-            models[r.rid] = (p, (C, H, W))
+            models[r.rid] = (ps, (C, H, W))
             results.append(Result(r.rid, "fit", r.arrival, now(), out, synth_psnr(out, r.image),
-                                  fb.losses()[0]))
+                                  np.mean(losses, axis=0)))
         else:
-            p, (C, H, W) = models[r.model]
+            ps, (C, H, W) = models[r.model]
             Ho, Wo = int(round(H * r.scale)), int(round(W * r.scale))
-            rr = Rasterizer(RasterDesc(Wo, Ho, C, tile, True, qmax, r.scale), p.K).bin(p)
-            y, _ = rr.render()
+            if len(ps) == 1:
+                rr = Rasterizer(RasterDesc(Wo, Ho, C, tile, True, qmax, r.scale),
+                                ps[0].K).bin(ps[0])
+                y, _ = rr.render()
+            else:
+                y = render_mean(ps, Wo, Ho, tile, qmax, r.scale)
             results.append(Result(r.rid, "render", r.arrival, now(), y.cpu().numpy()))
     return results
 
@@ -321,11 +359,12 @@ def latency_stats(results):
 
 
 def poisson_workload(n_fit, n_render, rate, seed=5, iters=500, sizes=None, noise_var=0.05,
-                     render_scales=(1.0, 4.0)):
+                     render_scales=(1.0, 4.0), mm_models=1):
     """Fit requests with sizes from `sizes` (default: the ragged size
     distribution, 128x96 .. 1920x1080), half of them denoising requests with
-    N(0, noise_var) added; render requests on earlier fits at scales drawn
-    from U[render_scales]; Poisson arrivals at `rate` per second."""
+    N(0, noise_var) added (MM-RSMoE with `mm_models` models when > 1);
+    render requests on earlier fits at scales drawn from U[render_scales];
+    Poisson arrivals at `rate` per second."""
     rng = np.random.default_rng(seed)
     sizes = sizes or synth.ragged_sizes(n_fit, seed)
     n = n_fit + n_render
@@ -344,7 +383,8 @@ def poisson_workload(n_fit, n_render, rate, seed=5, iters=500, sizes=None, noise
             den = (len(fit_ids) % 2) == 1
             if den:
                 img = (img + rng.normal(0.0, np.sqrt(noise_var), img.shape)).astype(np.float32)
-            reqs.append(FitRequest(i, img, iters, denoise=den, arrival=float(a), seed=i))
+            reqs.append(FitRequest(i, img, iters, denoise=den, arrival=float(a), seed=i,
+                                   models=mm_models if den else 1))
             fit_ids.append(i)
         else:
             reqs.append(RenderRequest(i, int(rng.choice(fit_ids)),

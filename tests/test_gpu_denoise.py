@@ -164,3 +164,29 @@ def test_mm_pipeline_deterministic_mode_is_reproducible():
         y, _ = denoise.mm_rsmoe(tn, ms, 20, deterministic=True)
         outs.append(y)
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("scale,tile", [(1.0, 16), (1.5, 8), (2.0, 16), (3.25, 32)])
+def test_standalone_render_mean_at_scale(scale, tile):
+    """smoe_render_mean: separate models on a raster `scale` times finer
+    (the resampled MM-RSMoE result), against the oracle's mean of the
+    scale-s renders; at scale 1 it equals the fit batch's fused render."""
+    W, H, C = 40, 30, 3
+    ps = [rand_params(700 + h, C, 18 + 5 * h, True) for h in range(3)]
+    Wo, Ho = int(round(W * scale)), int(round(H * scale))
+    models = [api.SMoEParams.from_numpy(p) for p in ps]
+    y = api.render_mean(models, Wo, Ho, tile=tile, scale=scale).cpu().numpy()
+    ref, sc = om.render_mean([om.Model(Wo, Ho, C, p.mu, p.chol, p.ea, p.eW, tile=tile,
+                                       scale=scale) for p in ps], with_scale=True)
+    assert np.all(np.abs(y - ref) <= RTOL_Y * sc)
+    if scale == 1.0:
+        yb, _ = fused_gpu(ps, W, H, C, tile)
+        assert np.array_equal(y, yb.cpu().numpy())
+
+
+def test_standalone_render_mean_grows_its_pair_buffer():
+    ps = [rand_params(720 + h, 3, 40, True) for h in range(2)]
+    models = [api.SMoEParams.from_numpy(p) for p in ps]
+    a = api.render_mean(models, 64, 48, tile=8, pair_cap=8)
+    b = api.render_mean(models, 64, 48, tile=8)
+    assert torch.equal(a, b)

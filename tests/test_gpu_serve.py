@@ -30,7 +30,9 @@ def requests():
         den = i == 1
         if den:
             img = (img + rng.normal(0, np.sqrt(0.05), img.shape)).astype(np.float32)
-        reqs.append(FitRequest(i, img, iters=n, sigma=3.0, denoise=den, arrival=0.0, seed=i))
+        # the denoising request is MM-RSMoE with four models (Sec. V-C)
+        reqs.append(FitRequest(i, img, iters=n, sigma=3.0, denoise=den, arrival=0.0, seed=i,
+                               models=4 if den else 1))
     reqs.append(RenderRequest(3, model=0, scale=2.0, arrival=0.0))
     reqs.append(RenderRequest(4, model=1, scale=1.5, arrival=0.0))
     reqs.append(RenderRequest(5, model=2, scale=3.25, arrival=0.0))
@@ -41,8 +43,8 @@ def test_served_results_equal_alone():
     reqs = requests()
     # room for the first two fits only: the third joins when the first leaves,
     # while the second continues in the re-formed batch
-    b = [serve.fit_bytes(3, r.image.shape[1], r.image.shape[2],
-                         r.image.shape[1] * r.image.shape[2] // 16) for r in reqs[:3]]
+    b = [r.models * serve.fit_bytes(3, r.image.shape[1], r.image.shape[2],
+                                    r.image.shape[1] * r.image.shape[2] // 16) for r in reqs[:3]]
     srv = serve.Server(b[0] + b[1] + 1, chunk=10, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))
     mixed = {r.rid: r for r in srv.run(reqs, realtime=False)}
     alone = {r.rid: r for r in serve.serve_plain(reqs, realtime=False,
