@@ -470,7 +470,8 @@ def run_serve(args):
     build.build()
     reqs = serve.poisson_workload(args.fits, args.renders, args.rate, iters=args.iters,
                                   sizes=None, mm_models=args.mm_models)
-    srv = serve.Server(args.budget_gb * (1 << 30), chunk=25)
+    srv = serve.Server(args.budget_gb * (1 << 30), chunk=25,
+                       max_pixels=int(args.max_mpx * 1e6) if args.max_mpx else None)
     t0 = time.perf_counter()
     res_b = srv.run(reqs, realtime=True)
     t_b = time.perf_counter() - t0
@@ -486,6 +487,7 @@ def run_serve(args):
         "metric": "serving: fit/render request latency p50/p99 and throughput, continuous "
                   "batching vs one request at a time", "mode": "serve",
         "mm_models_per_denoising_request": args.mm_models,
+        "max_mpx_in_flight": args.max_mpx or None,
         "requests": len(reqs), "fits": len(fits), "rate_per_s": args.rate, "iters": args.iters,
         "batched": {"wall_s": t_b, "req_per_s": len(reqs) / t_b,
                     "all": serve.latency_stats(res_b), "fit": serve.latency_stats(split(res_b, "fit")),
@@ -522,6 +524,8 @@ def main():
     ap.add_argument("--renders", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--max-mpx", type=float, default=16.0,
+                    help="serve: cap on megapixels (x models) in flight (0: HBM budget only)")
     ap.add_argument("--mm-models", type=int, default=4,
                     help="serve: MM-RSMoE models per denoising request")
     args = ap.parse_args()

@@ -105,8 +105,15 @@ class Server:
     """Continuous-batching server on one GPU (see the module docstring)."""
 
     def __init__(self, hbm_budget, tile=16, lr=synth.PAPER_LR, chunk=25, graphs=True,
-                 persistent=False, qmax=9.0, deterministic=True):
+                 persistent=False, qmax=9.0, deterministic=True, max_pixels=None):
+        """max_pixels: cap on the pixels in flight (image pixels x models over
+        the admitted fits); beyond the point where one batch fills the GPU,
+        more concurrency only stretches every request's iterations, so the
+        cap keeps the queue FIFO and the median latency down.  None: only
+        the HBM budget limits admission."""
         self.deterministic = deterministic
+        self.max_pixels = max_pixels
+        self.px_used = 0
         self.budget = int(hbm_budget)
         self.tile, self.lr, self.chunk = tile, lr, chunk
         self.graphs, self.persistent, self.qmax = graphs, persistent, qmax
@@ -222,12 +229,16 @@ class Server:
                 r = fits_q[0]
                 C, H, W = r.image.shape
                 need = r.models * fit_bytes(C, H, W, max(1, (H * W) // r.pixels_per_kernel))
+                px = r.models * H * W
                 if self.used + need > self.budget and (slots or inflight):
+                    break
+                if self.max_pixels and self.px_used + px > self.max_pixels and slots:
                     break
                 fits_q.popleft()
                 for s in self._make_slots(r):
                     self.used += s.nbytes
                     slots.append(s)
+                self.px_used += px
                 changed = True
                 self.events.append((now(), f"admit fit {r.rid}"))
             # start renders whose model is resident
@@ -268,6 +279,8 @@ class Server:
                         keep.append(s)
                 for rid, group in finished.items():
                     results.append(self._finish_fit(sorted(group, key=lambda g: g.member), now))
+                    r0 = group[0].req
+                    self.px_used -= r0.models * r0.image.shape[1] * r0.image.shape[2]
                     self.events.append((now(), f"finish fit {rid}"))
                 if len(keep) != len(slots):
                     slots = keep
