@@ -95,3 +95,21 @@ def test_failed_fit_surfaces_as_an_error(monkeypatch):
     srv = serve.Server(8 << 30, chunk=10)
     with pytest.raises(RuntimeError, match="fit status 3"):
         srv.run(reqs, realtime=False)
+
+
+def test_pixel_cap_serialises_admission():
+    """With room for one request's pixels in flight, each fit is admitted
+    only after the previous one finished, and the results are unchanged."""
+    reqs = [r for r in requests() if isinstance(r, FitRequest) and r.models == 1]
+    px = max(r.image.shape[1] * r.image.shape[2] for r in reqs)
+    srv = serve.Server(8 << 30, chunk=10, lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2), max_pixels=px)
+    mixed = {r.rid: r for r in srv.run(reqs, realtime=False)}
+    alone = {r.rid: r for r in serve.serve_plain(reqs, realtime=False,
+                                                 lr=(1e-2, 1e-3, 1e-2, 1e-2, 1e-2))}
+    ev = [e for _, e in srv.events]
+    order = [e for e in ev if e.startswith("admit fit") or e.startswith("finish fit")]
+    for i in range(0, len(order) - 1, 2):            # admit a, finish a, admit b, ...
+        assert order[i].startswith("admit") and order[i + 1].startswith("finish")
+        assert order[i].split()[-1] == order[i + 1].split()[-1]
+    for rid in mixed:
+        assert np.max(np.abs(alone[rid].output - mixed[rid].output)) <= TOL_Y
