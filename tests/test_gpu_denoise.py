@@ -101,7 +101,7 @@ def test_render_mean_of_one_model_is_its_render():
 
 
 def test_render_mean_grows_the_pair_buffer():
-    """A pair count above the buffer sets the capacity status; the driver
+    """A pair count above the buffer sets the capacity status; FitBatch
     grows the buffer and renders again, with the same result."""
     ps = [rand_params(900 + h, 3, 40, True) for h in range(3)]
     y_small, fb = fused_gpu(ps, 64, 48, 3, 8, pair_cap=16)
