@@ -226,7 +226,13 @@ def run_reference(args):
     import oracle
     oracle.build()
     wl = synth.rgb_2048()
+    # The dense oracle's cost per step grows as crop^4 (pixels x kernels); take
+    # the largest crop that keeps the whole run near 90 s (0.22 s per 256^2
+    # step on 16 cores), unless --ref-crop is given.
     size = args.ref_crop
+    if not size:
+        n = args.steps + args.warmup
+        size = next((c for c in (256, 192, 128, 96, 64) if n * 0.22 * (c / 256) ** 4 <= 90.0), 64)
     for _ in range(args.warmup):
         oracle_sample(wl, size)
     tot_pairs, tot_s, thr, kc = 0, 0.0, 1, 0
@@ -508,7 +514,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-crop", type=int, default=512)
-    ap.add_argument("--ref-crop", type=int, default=256)
+    ap.add_argument("--ref-crop", type=int, default=0,
+                    help="reference arm crop side (0: sized so the run takes about 90 s)")
     ap.add_argument("--binned-crop", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--mode", default="fit",
