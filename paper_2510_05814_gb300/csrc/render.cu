@@ -60,6 +60,12 @@ constexpr int kThreads = kNW * 32;
 #define SMOE_FWD_UNROLL 4
 #endif
 constexpr int kMinBlocks = SMOE_MIN_BLOCKS;
+// The forward-only kernels (render, fused mean) need fewer registers than
+// the backward: one more resident CTA per SM measured faster for them.
+#ifndef SMOE_MIN_BLOCKS_FWD
+#define SMOE_MIN_BLOCKS_FWD 5
+#endif
+constexpr int kMinBlocksFwd = SMOE_MIN_BLOCKS_FWD;
 
 template <int C, bool LIN>
 struct Rec {
@@ -327,7 +333,7 @@ __device__ __forceinline__ bool lane_pixels(int bi, int &row, int &col) {
 }
 
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(const __grid_constant__ Geo g, Bufs w,
+__global__ void __launch_bounds__(kThreads, kMinBlocksFwd) k_render(const __grid_constant__ Geo g, Bufs w,
                                                         float *__restrict__ y,
                                                         float *__restrict__ inv_d) {
     using G = Geom<C, T>;
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render(const __grid_co
 // is deterministic, and B = 1 gives k_render's output bit for bit.  The grid
 // covers the tiles of one image; image b's tiles follow image b-1's.
 template <int C, bool LIN, int T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_mean(const __grid_constant__ Geo g, Bufs w,
+__global__ void __launch_bounds__(kThreads, kMinBlocksFwd) k_render_mean(const __grid_constant__ Geo g, Bufs w,
                                                              float *__restrict__ y) {
     using G = Geom<C, T>;
     if (status_bad(w.status)) return;
