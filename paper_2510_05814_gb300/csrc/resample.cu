@@ -92,11 +92,12 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
         const float *r = rec + (int64_t)pair_k[q] * S;
         const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
         const float c = __ldg(r + 4), lp = __ldg(r + 5);
-        const float dx = __fsub_rn(p.x, r0.x);
         const float dy = __fsub_rn(p.y, r0.y);
-        const float tb = __fmul_rn(r0.w, dy);
         const float z1 = __fmul_rn(c, dy);
         const float u = __fmul_rn(z1, z1);
+        if (!(u <= qmax)) continue;          // q = fma(z0, z0, u) >= u: not included
+        const float dx = __fsub_rn(p.x, r0.x);
+        const float tb = __fmul_rn(r0.w, dy);
         float z0;
         const float qv = q_of(r0.z, dx, tb, u, z0);
         if (!(qv <= qmax)) continue;
