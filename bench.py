@@ -46,8 +46,8 @@ KERNELS_PER_STEP = 9
 # From one ncu capture of the fused tile kernel on this workload (profiles/):
 # DRAM bytes per launch and pipe utilisation; valid only while render.cu's
 # code (comments and whitespace aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "f92a7e4924d304f38b5dd34663f302c7c51f4ac336576f2c0e4e2a0756b74426",
-       "bytes_per_launch": 104.363264e6, "fma_pipe_active": 0.660, "issue_active": 0.623,
+NCU = {"render_cu_code_sha256": "84c8da3451bb37a21d8a73401d633741543408e1f01963cf7e08879a8cfcbbf3",
+       "bytes_per_launch": 105.402112e6, "fma_pipe_active": 0.660, "issue_active": 0.624,
        "xu_active": 0.142}
 
 
