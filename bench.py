@@ -46,9 +46,9 @@ KERNELS_PER_STEP = 9
 # From one ncu capture of the fused tile kernel on this workload (profiles/):
 # DRAM bytes per launch and pipe utilisation; valid only while render.cu's
 # code (comments and whitespace aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "84c8da3451bb37a21d8a73401d633741543408e1f01963cf7e08879a8cfcbbf3",
-       "bytes_per_launch": 105.402112e6, "fma_pipe_active": 0.660, "issue_active": 0.624,
-       "xu_active": 0.142}
+NCU = {"render_cu_code_sha256": "023a846244615376ce0e0d757481649c77f809707901515cfd6718cc83e15ca3",
+       "bytes_per_launch": 105.25824e6, "fma_pipe_active": 0.610, "issue_active": 0.600,
+       "xu_active": 0.129}
 
 
 def issue_rates():

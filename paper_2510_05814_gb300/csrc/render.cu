@@ -4,11 +4,11 @@
 //
 // One CTA (4 warps) per tile.  The tile's kernel list is processed in chunks
 // of up to NCH kernels; each chunk is staged in shared memory: the kernel's
-// prepared record and a ROW MASK, bit r set iff row r of the tile can hold an
-// included pixel.  The row test is exact: with the predicate's own FP32
-// values, q32 = fma(z0, z0, u) >= u = (c dy)^2 for every pixel of the row, so
-// a row with u > q_max holds no included pixel and skipping it changes no
-// result.
+// prepared record and a ROW MASK, bit r clear only where row r of the tile
+// holds no included pixel.  The row test evaluates the predicate's own FP32
+// value at the row's minimising column (see stage_chunk), so skipping the
+// clear rows changes no result; a listed kernel whose ellipse misses the
+// tile's pixels has an empty mask and costs only its staging.
 //
 // Forward (pixel-major): a warp owns a band of 64 pixels (2 adjacent pixels
 // per lane, 64/T rows) and walks the chunk, skipping every kernel whose mask
@@ -144,19 +144,47 @@ __device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const T
         if (q == 0) sm.kid[j] = kid;
     }
     __syncthreads();
-    // Row masks: u = (c dy)^2 with the predicate's FP32 operations.
-    for (int j = threadIdx.x; j < nc; j += kThreads) {
-        const float my = sm.rec[j * R::SS + 1], c = sm.rec[j * R::SS + 4];
+    // Row masks: bit r is clear only if no pixel of row r inside the tile
+    // passes the predicate, evaluated with the render's own FP32 operations
+    // q32 = fma(z0, z0, u), z0 = fma(a, x - mx, b dy), u = (c dy)^2.  Along
+    // a row z0 is monotone in the column (each operation rounds
+    // monotonically) and q32 is monotone in |z0|, so where z0 has one sign at
+    // the tile's first and last column the row's least q32 is fma(zm, zm, u),
+    // zm = min |z0| of those two columns, exactly.  Where the sign changes
+    // inside the tile the row keeps the test u <= q_max (q32 >= u): a
+    // superset, nearly always live anyway.  T / 8 adjacent lanes share a
+    // kernel, each taking 8 of its rows; every lane of a warp runs every round.
+    {
+        constexpr int LPK = T / 8;                         // lanes per kernel
+        const int lane = threadIdx.x & 31;
         const float y0f = (float)ti.y0 + 0.5f;
-        uint32_t m = 0;
+        const float xl = (float)ti.x0 + 0.5f;              // first and last column centres
+        const float xr = (float)ti.x0 + ((float)T - 0.5f);
+        for (int base = threadIdx.x & ~31; base < LPK * nc; base += kThreads) {
+            const int i = base + lane;
+            const int j = i < LPK * nc ? i / LPK : 0;
+            const int r0 = (i % LPK) * 8;
+            const float *rj = sm.rec + j * R::SS;
+            const float mx = rj[0], my = rj[1], a = rj[2], b = rj[3], c = rj[4];
+            const float dxl = __fsub_rn(xl, mx), dxr = __fsub_rn(xr, mx);
+            uint32_t m = 0;
 #pragma unroll
-        for (int r = 0; r < T; ++r) {
-            const float dy = __fsub_rn(__fadd_rn(y0f, (float)r), my);
-            const float z1 = __fmul_rn(c, dy);
-            const float u = __fmul_rn(z1, z1);
-            m |= (u <= g.qmax ? 1u : 0u) << r;
+            for (int rr = 0; rr < 8; ++rr) {
+                const float dy = __fsub_rn(__fadd_rn(y0f, (float)(r0 + rr)), my);
+                const float t = __fmul_rn(b, dy);
+                const float z1 = __fmul_rn(c, dy);
+                const float u = __fmul_rn(z1, z1);
+                const float zl = __fmaf_rn(a, dxl, t), zr = __fmaf_rn(a, dxr, t);
+                const float zm = fminf(fabsf(zl), fabsf(zr));
+                const bool one_sign = (zl >= 0.0f) == (zr >= 0.0f);
+                const float qm = one_sign ? __fmaf_rn(zm, zm, u) : u;
+                m |= (qm <= g.qmax ? 1u : 0u) << rr;
+            }
+            m <<= r0;
+#pragma unroll
+            for (int o = 1; o < LPK; o <<= 1) m |= __shfl_xor_sync(0xffffffffu, m, o);
+            if (i % LPK == 0 && i < LPK * nc) sm.mask[j] = m;
         }
-        sm.mask[j] = m;
     }
     __syncthreads();
 }
