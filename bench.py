@@ -568,7 +568,8 @@ def main():
     T = wl.tile
     tgt = torch.tensor(wl.target, device="cuda")
     params = api.SMoEParams.from_numpy(wl.params)
-    total_iters = args.warmup + 2 * args.steps + 4
+    n_phase = min(args.steps, 200)               # eager steps timed phase by phase
+    total_iters = args.warmup + 2 * args.steps + n_phase + 5
     fb = FitBatch([tgt], [params], total_iters, lr=synth.PAPER_LR, tile=T, qmax=wl.qmax,
                   hist=total_iters)
     desc = api.RasterDesc(W, H, C, T, True, wl.qmax, 1.0)
@@ -587,30 +588,43 @@ def main():
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # The step as FitBatch.run(graph_iters=...) runs it: one CUDA-graph replay
+    # of a whole fit iteration (its 9 kernels), L2 flushed before each step.
+    graph = fb.capture(1)
+    graph.replay()                              # one untimed replay
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    pev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_phase)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         for s in range(args.steps):
             flush.zero_()                       # L2 flush outside the timed region
-            e = ev[s]
-            e[0].record(stream)
-            fb.phase(0)
-            e[1].record(stream)
-            fb.phase(1)
-            e[2].record(stream)
-            fb.phase(2)
-            e[3].record(stream)
+            ev[s][0].record(stream)
+            graph.replay()
+            ev[s][1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    # the same step launched phase by phase (eager), for the breakdown
+    for s in range(n_phase):
+        flush.zero_()
+        e = pev[s]
+        e[0].record(stream)
+        fb.phase(0)
+        e[1].record(stream)
+        fb.phase(1)
+        e[2].record(stream)
+        fb.phase(2)
+        e[3].record(stream)
+    torch.cuda.synchronize()
     st = fb.status_code()
     assert st == 0, f"fit status {st}"
-    bin_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    tile_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    adam_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    bin_ms = [e[0].elapsed_time(e[1]) for e in pev]
+    tile_ms = [e[1].elapsed_time(e[2]) for e in pev]
+    adam_ms = [e[2].elapsed_time(e[3]) for e in pev]
+    eager_ms = [e[0].elapsed_time(e[3]) for e in pev]
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     pairs1, lists1, inrange1 = pairs_now()
     pairs_step = 0.5 * (pairs0 + pairs1)
     inrange_step = 0.5 * (inrange0 + inrange1)
@@ -645,7 +659,7 @@ def main():
                 ready[nxt].record(cstream)
         stream.wait_event(ready[cur])
         fb.set_target(0, bufs[cur])
-        it = int(args.warmup + args.steps + s)
+        it = int(args.warmup + 1 + args.steps + n_phase + s)
         fb.launch(1)
         freed[cur].record(stream)
         host_loss.copy_(fb.loss[0, it:it + 1], non_blocking=True)
@@ -729,6 +743,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "image": f"{W}x{H}x{C}", "K": params.K, "tile": T,
                        "l2": "flushed (256 MiB write, untimed) before every timed step",
+                       "launch": "one CUDA-graph replay of the whole fit iteration per step "
+                                 "(the FitBatch.run(graph_iters=...) path)",
                        "parallelism": f"replicas x{world}",
                        "pairs_per_step": int(pairs_step), "list_pairs": int(lists1),
                        "in_range_pairs_per_step": int(inrange_step)},
@@ -751,7 +767,10 @@ def main():
             "in_range": {"Gpairs_per_s": inrange_step / tile_s / 1e9,
                          "fraction_of_listed": inrange_step / pairs_step},
             "phases_ms": {"bin": statistics.mean(bin_ms), "fused_tiles": statistics.mean(tile_ms),
-                          "adam": statistics.mean(adam_ms)},
+                          "adam": statistics.mean(adam_ms), "eager_step": statistics.mean(eager_ms),
+                          "steps": n_phase,
+                          "how": "the same step launched phase by phase (no graph), "
+                                 "CUDA events between the phases"},
             "fit_iters_per_s": args.steps / tot_s,
             "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
                              "Gpairs_per_s": sr_pairs / sr_ms / 1e6},
@@ -764,6 +783,8 @@ def main():
                     "d2h_bytes_per_step": 8,
                     "copies": "pinned host target -> device each step on a copy stream "
                               "(double buffer, overlapping the previous step); loss -> host",
+                    "launch": "FitBatch.launch(1) per step (no graph: the target buffer "
+                              "alternates)",
                     "l2": "not flushed: steps back to back, as a caller runs them"},
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clocks,

@@ -53,25 +53,37 @@ __global__ void k_adam_soa(int64_t K, int C, int has_w, int has_pi, smoe_params 
     }
 }
 
+// x^n by squaring: FP64 multiplies only (no transcendental, whose FP64
+// form is slow on this part); relative error about 2 log2(n) ulp.
+__device__ __forceinline__ double ipow(double x, uint32_t n) {
+    double r = 1.0;
+    while (n) {
+        if (n & 1u) r *= x;
+        x *= x;
+        n >>= 1;
+    }
+    return r;
+}
+
 // Per-image Adam coefficients of the current step, formed in FP64 and rounded
 // once: the four step sizes lr_g / (1 - b1^t) (the centre rate follows the
-// exponential schedule) and 1 / sqrt(1 - b2^t).  Threads stride over images.
+// exponential schedule lr_mu0 (lr_mu1 / lr_mu0)^(it / (iters - 1)), i.e.
+// lr_mu0 rho^it) and 1 / sqrt(1 - b2^t).  Threads stride over images.
 __device__ void adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
                            float *coef) {
     for (int b = threadIdx.x; b < g.B; b += blockDim.x) {
         const ImgDev &im = img_of(g, b);
         const int32_t it = step[b];
-        const double t = (double)(it + 1);
-        const double bc1 = 1.0 - pow(b1, t);
-        const double f = im.iters > 1 ? (double)it / (double)(im.iters - 1) : 0.0;
-        const double lr_mu =
-            im.lr_mu0 > 0.0f ? (double)im.lr_mu0 * pow((double)im.lr_mu1 / im.lr_mu0, f) : 0.0;
+        const uint32_t t = (uint32_t)it + 1u;
+        const double bc1 = 1.0 - ipow(b1, t);
+        const double bc2 = 1.0 - ipow(b2, t);
+        const double lr_mu = im.lr_mu0 > 0.0f ? (double)im.lr_mu0 * ipow(im.mu_rho, (uint32_t)it) : 0.0;
         float *c = coef + 8 * b;
         c[0] = (float)(lr_mu / bc1);
         c[1] = (float)(im.lr_chol / bc1);
         c[2] = (float)(im.lr_ea / bc1);
         c[3] = (float)(im.lr_eW / bc1);
-        c[4] = (float)(1.0 / sqrt(1.0 - pow(b2, t)));
+        c[4] = (float)(1.0 / sqrt(bc2));
         c[5] = (float)(im.lr_pi / bc1);
     }
 }
@@ -83,24 +95,132 @@ __global__ void k_adam_coefs(const __grid_constant__ Geo g, const int32_t *step,
 
 // Fit: raw per-kernel sums -> gradients (see render.cu) -> Adam on the 5 + C
 // (+ 2C, + 1 with gate weights) parameters of the kernel; zeroes the sums.
-// The sums and the prepared record are loaded whole (float4) into registers.
-// The last CTA to finish advances every running image's step counter and
-// forms the coefficients of the next step.
+// Two phases per CTA of kAdamThreads kernels: (1) each thread turns its
+// kernel's sums and prepared record (loaded whole, float4) into gradients in
+// shared memory, laid out like the parameter arrays; (2) the CTA updates the
+// parameters and moments group by group, consecutive threads on consecutive
+// elements, so every global access is coalesced.  The last CTA to finish
+// advances every running image's step counter and forms the coefficients of
+// the next step.
+constexpr int kAdamThreads = 256;
+
+// Adam on one parameter group of a CTA's kernels (N values per kernel):
+// gradients in shared memory (gs[e], e = t N + j for kernel k0 + t), `img`
+// the kernel's image or -1, `ptr` picks the group's array from a parameter
+// set, `ci` its step-size coefficient.
+template <int N, typename F>
+__device__ __forceinline__ void adam_group(const Geo &g, const Betas &be, const float *coef,
+                                           int64_t k0, const int32_t *img, const float *gs,
+                                           int ci, F ptr) {
+    float pv[N], mv[N], vv[N];
+    float *pp[N], *mp[N], *vp[N];
+    int bb[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int e = threadIdx.x + i * kAdamThreads;
+        const int t = e / N;
+        bb[i] = img[t];
+        pp[i] = nullptr;
+        if (bb[i] >= 0) {
+            const ImgDev &im = img_of(g, bb[i]);
+            float *base = ptr(im.p);
+            if (base) {
+                const int64_t x = (k0 + t - im.k_off) * N + (e - t * N);
+                pp[i] = base + x;
+                mp[i] = ptr(im.m) + x;
+                vp[i] = ptr(im.v) + x;
+                pv[i] = *pp[i];
+                mv[i] = *mp[i];
+                vv[i] = *vp[i];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (!pp[i]) continue;
+        const float *cf = coef + 8 * bb[i];
+        const AdamK kk{be, cf[ci], cf[4]};
+        adam1(pv[i], gs[threadIdx.x + i * kAdamThreads], mv[i], vv[i], kk);
+        *pp[i] = pv[i];
+        *mp[i] = mv[i];
+        *vp[i] = vv[i];
+    }
+}
+
+// Phase 2 for a CTA whose kernels all belong to one running image (base
+// pointers uniform): every group's p, m and v values are loaded before any
+// is stored, one memory round trip for the whole update.
 template <int C, bool LIN>
-__global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2,
-                           Betas be, int32_t *step, uint32_t *done, float *coef) {
+__device__ __forceinline__ void adam_uniform(const ImgDev &im, const Betas &be, const float *cf,
+                                             int64_t kl0, const float *gsm, bool has_pi) {
+    constexpr int NW = LIN ? 2 * C : 0;
+    constexpr int NT = 2 + 3 + C + NW + 1;                 // values per thread (logpi last)
+    const int tid = threadIdx.x;
+    float pv[NT], mv[NT], vv[NT];
+    // element i of the thread: group, elements per kernel n, index j within it
+    auto elem = [&](int i, const smoe_params &q, float *&ptr, int64_t &x) {
+        int n, j, base = 0;
+        if (i < 2) { ptr = q.mu; n = 2; j = i; }
+        else if (i < 5) { ptr = q.chol; n = 3; j = i - 2; base = 2 * kAdamThreads; }
+        else if (i < 5 + C) { ptr = q.ea; n = C; j = i - 5; base = 5 * kAdamThreads; }
+        else if (i < 5 + C + NW) { ptr = q.eW; n = NW ? NW : 1; j = i - 5 - C; base = (5 + C) * kAdamThreads; }
+        else { ptr = q.logpi; n = 1; j = 0; base = (5 + C + NW) * kAdamThreads; }
+        const int e = tid + j * kAdamThreads;               // element of the CTA's range
+        x = kl0 * n + e;
+        return base + e;                                    // its gradient in shared memory
+    };
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        float *pp; int64_t x;
+        elem(i, im.p, pp, x);
+        if (i == NT - 1 && !has_pi) continue;
+        float *mp, *vp; int64_t xm, xv;
+        elem(i, im.m, mp, xm);
+        elem(i, im.v, vp, xv);
+        pv[i] = pp[x]; mv[i] = mp[xm]; vv[i] = vp[xv];
+    }
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        if (i == NT - 1 && !has_pi) continue;
+        float *pp, *mp, *vp; int64_t x, xm, xv;
+        const int gi = elem(i, im.p, pp, x);
+        elem(i, im.m, mp, xm);
+        elem(i, im.v, vp, xv);
+        const int ci = i < 2 ? 0 : i < 5 ? 1 : i < 5 + C ? 2 : i < 5 + C + NW ? 3 : 5;
+        const AdamK kk{be, cf[ci], cf[4]};
+        adam1(pv[i], gsm[gi], mv[i], vv[i], kk);
+        pp[x] = pv[i]; mp[xm] = mv[i]; vp[xv] = vv[i];
+    }
+}
+
+template <int C, bool LIN>
+__global__ void __launch_bounds__(kAdamThreads, 2)
+k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2, Betas be, int32_t *step,
+           uint32_t *done, float *coef) {
     constexpr int E = LIN ? 3 : 1;
     constexpr int S = (7 + C * E + 3) & ~3;       // record stride (floats)
     constexpr int GS = (6 + C * E + 3) & ~3;      // sums stride (floats)
     constexpr int PI = 5 + C * E;                 // dL/dlogpi slot
+    constexpr int NW = LIN ? 2 * C : 0;           // slopes per kernel
+    // gradient groups in shared memory: mu (2), chol (3), ea (C), eW (2C), logpi (1)
+    constexpr int O_MU = 0, O_CH = O_MU + 2 * kAdamThreads, O_EA = O_CH + 3 * kAdamThreads;
+    constexpr int O_EW = O_EA + C * kAdamThreads, O_PI = O_EW + NW * kAdamThreads;
+    __shared__ float gsm[O_PI + kAdamThreads];
+    __shared__ int32_t kimg[kAdamThreads];        // the kernel's image, -1: nothing to update
+    __shared__ bool last;
     if (status_bad(w.status)) return;
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < g.K_total) {
-        const int b = img_by_kernel(g, k);
-        const ImgDev &im = img_of(g, b);
-        const int32_t it = step[b];
-        if (it < im.iters) {
-            const int64_t kl = k - im.k_off;
+    const int tid = threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.x * kAdamThreads;
+    const int64_t k = k0 + tid;
+    {
+        int bk = -1;
+        if (k < g.K_total) {
+            const int b = img_by_kernel(g, k);
+            if (step[b] < img_of(g, b).iters) bk = b;
+        }
+        kimg[tid] = bk;
+        if (bk >= 0) {
+            const ImgDev &im = img_of(g, bk);
             // A kernel listed in no tile touched no pixel: its gradient is 0
             // (and must not become inf * 0 for non-finite parameters).
             const int4 rc = w.rect[k];
@@ -126,58 +246,48 @@ __global__ void k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, dou
                 const float4 v = rec[q];
                 r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
             }
-            const float *cf = coef + 8 * b;
-            const float isb2 = cf[4];
-            const AdamK kmu{be, cf[0], isb2}, kch{be, cf[1], isb2}, kea{be, cf[2], isb2};
-            const AdamK kew{be, cf[3], isb2}, kpi{be, cf[5], isb2};
             float gmx = 0.f, gmy = 0.f;
             if (listed) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                const int64_t x = kl * C + ch;
-                float pv = im.p.ea[x], mv = im.m.ea[x], vv = im.v.ea[x];
-                adam1(pv, s[5 + ch], mv, vv, kea);
-                im.p.ea[x] = pv; im.m.ea[x] = mv; im.v.ea[x] = vv;
+                gsm[O_EA + tid * C + ch] = s[5 + ch];
                 if (LIN) {
                     if (listed) {
                         gmx -= r[7 + ch * E + 1] * s[5 + ch];
                         gmy -= r[7 + ch * E + 2] * s[5 + ch];
                     }
 #pragma unroll
-                    for (int d = 0; d < 2; ++d) {
-                        const int64_t xw = x * 2 + d;
-                        float pw = im.p.eW[xw], mw = im.m.eW[xw], vw = im.v.eW[xw];
-                        adam1(pw, s[5 + (1 + d) * C + ch], mw, vw, kew);
-                        im.p.eW[xw] = pw; im.m.eW[xw] = mw; im.v.eW[xw] = vw;
-                    }
+                    for (int d = 0; d < 2; ++d) gsm[O_EW + tid * NW + 2 * ch + d] = s[5 + (1 + d) * C + ch];
                 }
             }
-            const float gm[2] = {gmx * (float)im.W, gmy * (float)im.H};
+            gsm[O_MU + 2 * tid] = gmx * (float)im.W;
+            gsm[O_MU + 2 * tid + 1] = gmy * (float)im.H;
 #pragma unroll
-            for (int d = 0; d < 2; ++d) {
-                float pv = im.p.mu[2 * kl + d], mv = im.m.mu[2 * kl + d], vv = im.v.mu[2 * kl + d];
-                adam1(pv, gm[d], mv, vv, kmu);
-                im.p.mu[2 * kl + d] = pv; im.m.mu[2 * kl + d] = mv; im.v.mu[2 * kl + d] = vv;
-            }
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                float pv = im.p.chol[3 * kl + d], mv = im.m.chol[3 * kl + d];
-                float vv = im.v.chol[3 * kl + d];
-                adam1(pv, -s[d], mv, vv, kch);
-                im.p.chol[3 * kl + d] = pv; im.m.chol[3 * kl + d] = mv; im.v.chol[3 * kl + d] = vv;
-            }
-            if (im.p.logpi) {                              // gate weight: dL/dlogpi = S0
-                float pv = im.p.logpi[kl], mv = im.m.logpi[kl], vv = im.v.logpi[kl];
-                adam1(pv, s[PI], mv, vv, kpi);
-                im.p.logpi[kl] = pv; im.m.logpi[kl] = mv; im.v.logpi[kl] = vv;
-            }
+            for (int d = 0; d < 3; ++d) gsm[O_CH + 3 * tid + d] = -s[d];
+            gsm[O_PI + tid] = s[PI];                       // dL/dlogpi = S0
             if (!w.part && listed)     // an unlisted kernel's sums received nothing: still 0
 #pragma unroll
                 for (int q = 0; q < GS / 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
+    // One image for the whole CTA (and it is running): the single-round-trip update.
+    const int b0 = kimg[0];
+    if (__syncthreads_and(kimg[tid] == b0 && b0 >= 0)) {
+        const ImgDev &im = img_of(g, b0);
+        adam_uniform<C, LIN>(im, be, coef + 8 * b0, k0 - im.k_off, gsm, im.p.logpi != nullptr);
+    } else {
+    // Phase 2: group by group, element e of the CTA's range is parameter
+    // e % N of kernel k0 + e / N; a thread loads its N elements of p, m and v
+    // before it stores any.
+    adam_group<2>(g, be, coef, k0, kimg, gsm + O_MU, 0, [](const smoe_params &q) { return q.mu; });
+    adam_group<3>(g, be, coef, k0, kimg, gsm + O_CH, 1, [](const smoe_params &q) { return q.chol; });
+    adam_group<C>(g, be, coef, k0, kimg, gsm + O_EA, 2, [](const smoe_params &q) { return q.ea; });
+    if (LIN)
+        adam_group<NW ? NW : 1>(g, be, coef, k0, kimg, gsm + O_EW, 3,
+                                [](const smoe_params &q) { return q.eW; });
+    adam_group<1>(g, be, coef, k0, kimg, gsm + O_PI, 5, [](const smoe_params &q) { return q.logpi; });
+    }
     // Step counters advance once every CTA has read them.
-    __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -238,13 +348,13 @@ cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const s
 
 cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, double eps,
                             int32_t *step, uint32_t *done, float *coef, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((g.K_total + 255) / 256);
+    const unsigned blocks = (unsigned)((g.K_total + kAdamThreads - 1) / kAdamThreads);
     if (blocks == 0) return cudaSuccess;
     const Betas be{(float)b2, (float)(1.0 - b1), (float)(1.0 - b2), (float)eps};
-    if (g.C == 1 && !g.linear) k_fit_adam<1, false><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
-    else if (g.C == 1) k_fit_adam<1, true><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
-    else if (!g.linear) k_fit_adam<3, false><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
-    else k_fit_adam<3, true><<<blocks, 256, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    if (g.C == 1 && !g.linear) k_fit_adam<1, false><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else if (g.C == 1) k_fit_adam<1, true><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else if (!g.linear) k_fit_adam<3, false><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    else k_fit_adam<3, true><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
     return cudaGetLastError();
 }
 

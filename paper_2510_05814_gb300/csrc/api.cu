@@ -169,6 +169,9 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
         d.lr_eW = im.lr_eW;
         d.lr_pi = im.lr_pi;
         if (!(d.lr_mu0 > 0.0f)) d.lr_mu0 = d.lr_mu1 = 0.0f;
+        d.mu_rho = d.lr_mu0 > 0.0f && d.iters > 1
+                       ? std::pow((double)d.lr_mu1 / (double)d.lr_mu0, 1.0 / (double)(d.iters - 1))
+                       : 1.0;
         K_total += im.p.K;
         t_total += (int64_t)d.tiles_x * d.tiles_y;
     }

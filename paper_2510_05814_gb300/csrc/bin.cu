@@ -39,17 +39,33 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
     const int wdt = rect.z - rect.x + 1;
     const int n = valid && rect.x <= rect.z ? wdt * (rect.w - rect.y + 1) : 0;
     auto visit = [&](int64_t t, int32_t kid) {
-        if (SCATTER) {
-            const int slot = atomicAdd(&w.cursor[t], 1);
-            w.pair_tmp[(int64_t)w.tile_off[t] + slot] = kid;
-        } else {
-            atomicAdd(&w.tile_cnt[t], 1);
-        }
+        if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kid;
+        else atomicAdd(&w.tile_cnt[t], 1);
     };
     if (n <= kBig) {             // small rectangles: each lane walks its own
-        for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
-            for (int tx = rect.x; tx <= rect.z; ++tx)
-                visit(t_off + (int64_t)ty * tiles_x + tx, k);
+        if (SCATTER) {
+            // four slot claims in flight before their stores
+            int tx = rect.x;
+            int64_t row = t_off + (int64_t)rect.y * tiles_x;
+            for (int i = 0; i < n; i += 4) {
+                int slot[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    slot[u] = -1;
+                    if (i + u < n) {
+                        slot[u] = atomicAdd(&w.cursor[row + tx], 1);
+                        if (++tx > rect.z) { tx = rect.x; row += tiles_x; }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (slot[u] >= 0) w.pair_tmp[slot[u]] = k;
+            }
+        } else {
+            for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
+                for (int tx = rect.x; tx <= rect.z; ++tx)
+                    visit(t_off + (int64_t)ty * tiles_x + tx, k);
+        }
     }
     unsigned big = __ballot_sync(0xffffffffu, n > kBig);
     while (big) {
@@ -68,39 +84,63 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
     }
 }
 
-__global__ void k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
+__global__ void __launch_bounds__(256, 6) k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
     if (status_bad(w.status)) return;
     const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = k_raw < g.K_total;
     const int64_t k = valid ? k_raw : g.K_total - 1;   // inactive lanes mirror the last kernel
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
     const int64_t kl = k - im.k_off;                   // the image's own kernel index
-    // Kernel in output-pixel units, one rounding per operation.
-    float mx = __fmul_rn(im.p.mu[2 * kl], (float)im.W);
-    float my = __fmul_rn(im.p.mu[2 * kl + 1], (float)im.H);
+    // Every input is loaded before the first store (the record's stores may
+    // alias nothing, but the compiler cannot know that): one memory round
+    // trip per kernel instead of one per channel.
+    const float mu0 = im.p.mu[2 * kl], mu1 = im.p.mu[2 * kl + 1];
     float a = im.p.chol[3 * kl], b = im.p.chol[3 * kl + 1], c = im.p.chol[3 * kl + 2];
+    const float lp = im.p.logpi ? im.p.logpi[kl] : 0.0f;
+    float ex[3], w0[3], w1[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const bool on = ch < g.C;
+        ex[ch] = on ? im.p.ea[kl * g.C + ch] : 0.0f;
+        w0[ch] = on && g.linear ? im.p.eW[(kl * g.C + ch) * 2] : 0.0f;
+        w1[ch] = on && g.linear ? im.p.eW[(kl * g.C + ch) * 2 + 1] : 0.0f;
+    }
+    // Kernel in output-pixel units, one rounding per operation.
+    const float mx = __fmul_rn(mu0, (float)im.W);
+    const float my = __fmul_rn(mu1, (float)im.H);
     const bool scaled = g.scale != 1.0f;
     if (scaled) {
         a = __fdiv_rn(a, g.scale);
         b = __fdiv_rn(b, g.scale);
         c = __fdiv_rn(c, g.scale);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            w0[ch] = __fdiv_rn(w0[ch], g.scale);
+            w1[ch] = __fdiv_rn(w1[ch], g.scale);
+        }
     }
     if (valid) {
-        float *r = w.rec + k * g.S;
+        // record: [0..4] mx my a b c, [5] log2 pi, [6] 0, [7 + ch E + e] experts,
+        // zero-padded to S floats (S <= 16), written as float4
+        float r[16];
         r[0] = mx; r[1] = my; r[2] = a; r[3] = b; r[4] = c;
-        r[5] = im.p.logpi ? __fmul_rn(im.p.logpi[kl], kLog2e) : 0.0f;   // log2 pi
-        r[6] = 0.0f;
-        const int E = g.linear ? 3 : 1;
-        for (int ch = 0; ch < g.C; ++ch) {
-            r[7 + ch * E] = im.p.ea[kl * g.C + ch];
-            if (g.linear) {
-                float w0 = im.p.eW[(kl * g.C + ch) * 2], w1 = im.p.eW[(kl * g.C + ch) * 2 + 1];
-                if (scaled) { w0 = __fdiv_rn(w0, g.scale); w1 = __fdiv_rn(w1, g.scale); }
-                r[7 + ch * E + 1] = w0;
-                r[7 + ch * E + 2] = w1;
+        r[5] = __fmul_rn(lp, kLog2e);              // pi = 1 stores 0
+#pragma unroll
+        for (int x = 6; x < 16; ++x) r[x] = 0.0f;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            if (ch < g.C) {
+                if (g.linear) {
+                    r[7 + 3 * ch] = ex[ch]; r[8 + 3 * ch] = w0[ch]; r[9 + 3 * ch] = w1[ch];
+                } else {
+                    r[7 + ch] = ex[ch];
+                }
             }
         }
-        for (int x = 7 + g.C * E; x < g.S; ++x) r[x] = 0.0f;
+        float4 *dst = reinterpret_cast<float4 *>(w.rec + k * g.S);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (4 * q < g.S) dst[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
     }
 
     // Bounding box: square of half side r = sqrt(q_max * lambda_max(Sigma))
@@ -240,8 +280,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const int
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         if (base + i < n) {
-            tile_off[base + i] = (int32_t)(run < cap ? run : cap);
-            cursor[base + i] = 0;
+            const int32_t o = (int32_t)(run < cap ? run : cap);
+            tile_off[base + i] = o;
+            cursor[base + i] = o;                 // scatter cursor: the tile's first slot
         }
         run += v[i];
     }

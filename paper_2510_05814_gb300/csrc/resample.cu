@@ -54,7 +54,7 @@ __global__ void k_pt_tile(int64_t n, const float2 *__restrict__ xy, int W, int H
 }
 
 __global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
-                             const int32_t *__restrict__ off, int32_t *__restrict__ cursor,
+                             int32_t *__restrict__ cursor,
                              int32_t *__restrict__ order, const int32_t *status) {
     if (status_bad(status)) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -65,7 +65,7 @@ __global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
     int base = 0;
     if (lane == leader) base = atomicAdd(&cursor[t], __popc(peers));
     base = __shfl_sync(peers, base, leader);
-    order[off[t] + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+    order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;   // cursor starts at off[t]
 }
 
 // One thread per sorted in-image point: D = sum e_k, N_c = sum e_k m_kc over
@@ -196,7 +196,7 @@ cudaError_t launch_render_points(const Geo &g, const float *rec, const int32_t *
     e = launch_exscan(tiles, pb.cnt, pb.bsum, pb.off, pb.n_in, pb.n_long, pb.cursor, n,
                       const_cast<int32_t *>(status), st);
     if (e != cudaSuccess) return e;
-    k_pt_scatter<<<grid, kPtThreads, 0, st>>>(n, pb.pt_tile, pb.off, pb.cursor, pb.order, status);
+    k_pt_scatter<<<grid, kPtThreads, 0, st>>>(n, pb.pt_tile, pb.cursor, pb.order, status);
     const int S = g.S;
     if (g.C == 1 && !g.linear)
         launch_points_kernel<1, false>(grid, st, n, pb.n_in, p2, pb.order, pb.pt_tile, tile_off,

@@ -38,6 +38,7 @@ struct ImgDev {
     smoe_params p, m, v;
     int32_t iters;
     float lr_mu0, lr_mu1, lr_chol, lr_ea, lr_eW, lr_pi;
+    double mu_rho;         // per-iteration factor of the centre rate: (lr_mu1 / lr_mu0)^(1 / (iters - 1))
 };
 
 struct Geo {
@@ -159,7 +160,7 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st);
 cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
                           cudaStream_t st);
 // Exclusive prefix sum of n counters into off[0..n] (off[n] = min(total, cap),
-// *total = the sum, cursor[0..n) zeroed; a total above cap sets
+// *total = the sum, cursor[i] = off[i] (a scatter's first slot); a total above cap sets
 // SMOE_ERR_CAPACITY); needs ceil(n / 4096) entries of bsum.
 cudaError_t launch_exscan(int64_t n, const int32_t *cnt, long long *bsum, int32_t *off,
                           int64_t *total, int32_t *n_long, int32_t *cursor, int64_t cap,
