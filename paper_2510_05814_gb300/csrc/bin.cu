@@ -84,7 +84,109 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
     }
 }
 
-__global__ void __launch_bounds__(256, 6) k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
+// Per-warp aggregation of the walks.  A warp's 32 consecutive kernels are
+// mostly neighbours, so their rectangles overlap: when the union box of the
+// warp's rectangles (one image) holds at most kAggMax tiles and fewer tiles
+// than the rectangles' total, the warp visits each union tile once and adds
+// the number of its kernels covering it with one atomic; the scatter then
+// places the covering kernels at base + their rank in lane order.  Other
+// warps walk lane by lane (walk_rects).  Both passes take the same decision
+// from the same rectangles, so counts and slots agree.
+constexpr int kAggMax = 128;
+constexpr int kBinThreads = 256;
+
+struct WarpAgg {
+    union {
+        int4 rect[32];          // count: the warp's rectangles
+        struct {
+            int base[kAggMax];  // scatter, per union tile: first slot claimed for the warp
+            unsigned bal[kAggMax];   // and the lanes covering it
+        };
+    };
+};
+
+template <bool SCATTER>
+__device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, int64_t t_off,
+                                          int tiles_x, int32_t k, WarpAgg &wa) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool has = valid && rect.x <= rect.z && rect.y <= rect.w;
+    const unsigned any = __ballot_sync(full, has);
+    if (!any) return;
+    const int src = __ffs(any) - 1;
+    const int64_t t0 = __shfl_sync(full, t_off, src);
+    const bool one_image = __all_sync(full, !has || t_off == t0);
+    const int ux0 = __reduce_min_sync(full, has ? rect.x : 0x7fffffff);
+    const int uy0 = __reduce_min_sync(full, has ? rect.y : 0x7fffffff);
+    const int ux1 = __reduce_max_sync(full, has ? rect.z : -1);
+    const int uy1 = __reduce_max_sync(full, has ? rect.w : -1);
+    const int uw = ux1 - ux0 + 1;
+    const long long nu = (long long)uw * (uy1 - uy0 + 1);
+    const int own = has ? (rect.z - rect.x + 1) * (rect.w - rect.y + 1) : 0;
+    const unsigned total = __reduce_add_sync(full, (unsigned)min(own, 1 << 20));
+    if (!one_image || nu > kAggMax || nu >= (long long)total) {
+        walk_rects<SCATTER>(w, valid, rect, t_off, tiles_x, k);
+        return;
+    }
+    if (!SCATTER) {
+        // count: one union tile per lane, the warp's rectangles from shared memory
+        wa.rect[lane] = has ? rect : make_int4(1, 1, 0, 0);
+        __syncwarp();
+        for (int u = lane; u < (int)nu; u += 32) {
+            const int tx = ux0 + u % uw, ty = uy0 + u / uw;
+            int c = 0;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) {
+                const int4 r = wa.rect[l];
+                c += (r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w) ? 1 : 0;
+            }
+            if (c) atomicAdd(&w.tile_cnt[t0 + (int64_t)ty * tiles_x + tx], c);
+        }
+        __syncwarp();
+        return;
+    }
+    // Scatter: sweep the union box row by row, 32 tiles at a time: one ballot
+    // per tile of the lanes covering it; lane j keeps the ballot of the
+    // chunk's tile j and claims its popcount of slots.
+    const unsigned lower = (1u << lane) - 1u;
+    int u = 0, tx = ux0, ty = uy0;
+    bool row_in = has && rect.y <= ty && ty <= rect.w;
+    while (u < (int)nu) {
+        unsigned mine = 0;
+        int my_tx = 0, my_ty = 0;
+        const int n_chunk = min(32, (int)nu - u);
+        for (int j = 0; j < n_chunk; ++j) {
+            const unsigned bal = __ballot_sync(full, row_in && rect.x <= tx && tx <= rect.z);
+            if (lane == j) { mine = bal; my_tx = tx; my_ty = ty; }
+            if (++tx > ux1) {
+                tx = ux0;
+                ++ty;
+                row_in = has && rect.y <= ty && ty <= rect.w;
+            }
+        }
+        if (lane < n_chunk && mine) {
+            const int64_t t = t0 + (int64_t)my_ty * tiles_x + my_tx;
+            wa.base[u + lane] = atomicAdd(&w.cursor[t], __popc(mine));
+            wa.bal[u + lane] = mine;
+        }
+        u += n_chunk;
+    }
+    __syncwarp();
+    // each lane places its kernel in its own tiles: base + rank in lane order
+    if (has) {
+        for (int y = rect.y; y <= rect.w; ++y) {
+            const int ub = (y - uy0) * uw - ux0;
+            for (int x = rect.x; x <= rect.z; ++x) {
+                const int uu = ub + x;
+                w.pair_tmp[wa.base[uu] + __popc(wa.bal[uu] & lower)] = k;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kBinThreads, 4) k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
+    __shared__ WarpAgg agg[kBinThreads / 32];
     if (status_bad(w.status)) return;
     const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = k_raw < g.K_total;
@@ -188,7 +290,7 @@ __global__ void __launch_bounds__(256, 6) k_prep_bbox(const __grid_constant__ Ge
         }
     }
     if (valid) w.rect[k] = rect;
-    walk_rects<false>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k);
+    walk_warp<false>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
 }
 
 // Block-wide exclusive scan of one long long per thread (1024 threads).
@@ -288,14 +390,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(int64_t n, const int
     }
 }
 
-__global__ void k_scatter(const __grid_constant__ Geo g, Bufs w) {
+__global__ void __launch_bounds__(kBinThreads) k_scatter(const __grid_constant__ Geo g, Bufs w) {
+    __shared__ WarpAgg agg[kBinThreads / 32];
     if (status_bad(w.status)) return;
     const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = k_raw < g.K_total;
     const int64_t k = valid ? k_raw : g.K_total - 1;
     const int4 rect = w.rect[k];
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
-    walk_rects<true>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k);
+    walk_warp<true>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
 }
 
 __device__ int block_exscan_int(int v, int *total) {
@@ -475,8 +578,8 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * n, st);
     if (e != cudaSuccess) return e;
     if (g.K_total > 0) {
-        const unsigned gb = (unsigned)((g.K_total + 255) / 256);
-        k_prep_bbox<<<gb, 256, 0, st>>>(g, w);
+        const unsigned gb = (unsigned)((g.K_total + kBinThreads - 1) / kBinThreads);
+        k_prep_bbox<<<gb, kBinThreads, 0, st>>>(g, w);
     }
     const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.status);
@@ -485,8 +588,8 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     k_scan_down<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.tile_off, w.cursor,
                                              w.pair_cap, w.status);
     if (g.K_total > 0) {
-        const unsigned gb = (unsigned)((g.K_total + 255) / 256);
-        k_scatter<<<gb, 256, 0, st>>>(g, w);
+        const unsigned gb = (unsigned)((g.K_total + kBinThreads - 1) / kBinThreads);
+        k_scatter<<<gb, kBinThreads, 0, st>>>(g, w);
     }
     if (n > 0) {
         k_segsort_warp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, w);
