@@ -1,0 +1,159 @@
+"""GPU parity of the culling shortcuts against the oracle, through the C ABI.
+
+- Binning with warp-aggregated walks: kernels in grid order (a warp's 32
+  consecutive kernels are neighbours, so most warps count and scatter per
+  union tile) mixed with wide kernels that send their warp to the per-lane
+  walk; the lists stay bit-exact (Sec. IV-C, Eq. 5).
+- Row masks evaluated over the tile's columns: thin, tilted, mirrored
+  (a < 0), nearly degenerate and very narrow kernels whose ellipses graze
+  tile edges; the render (Eqs. 2-4) and the backward stay within the bars
+  against the dense oracle, which evaluates every pixel against every kernel.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as om  # noqa: E402
+from paper_2510_05814_gb300 import api, synth  # noqa: E402
+
+RTOL_Y = 1e-5
+RTOL_G = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_05814_gb300 import build
+    build.build()
+    om.build()
+
+
+def model(p, W, H, C, tile):
+    return om.Model(W, H, C, p.mu, p.chol, p.ea, p.eW, tile=tile)
+
+
+def lists_gpu(p, W, H, C, tile):
+    params = api.SMoEParams.from_numpy(p)
+    desc = api.RasterDesc(W, H, C, tile, p.eW is not None, 9.0, 1.0)
+    r = api.Rasterizer(desc, params.K).bin(params)
+    return params, r
+
+
+def aggregated_warps(ref_off, ref_pk, K, W, H, tile):
+    """From the oracle's lists: each kernel's tile rectangle, then the
+    number of warps (32 consecutive kernels) whose union box is compact
+    enough for the aggregated walk (at most 128 tiles and fewer than the
+    rectangles' total), and the number of warps that are not."""
+    tx = (W + tile - 1) // tile
+    x0 = np.full(K, 1 << 30); x1 = np.full(K, -1); y0 = np.full(K, 1 << 30); y1 = np.full(K, -1)
+    for t in range(len(ref_off) - 1):
+        ks = ref_pk[ref_off[t]:ref_off[t + 1]]
+        cx, cy = t % tx, t // tx
+        x0[ks] = np.minimum(x0[ks], cx); x1[ks] = np.maximum(x1[ks], cx)
+        y0[ks] = np.minimum(y0[ks], cy); y1[ks] = np.maximum(y1[ks], cy)
+    agg = other = 0
+    for w0 in range(0, K, 32):
+        s = slice(w0, min(w0 + 32, K))
+        has = x1[s] >= 0
+        if not has.any():
+            continue
+        area = ((x1[s] - x0[s] + 1) * (y1[s] - y0[s] + 1))[has].sum()
+        nu = (x1[s][has].max() - x0[s][has].min() + 1) * (y1[s][has].max() - y0[s][has].min() + 1)
+        if nu <= 128 and nu < area:
+            agg += 1
+        else:
+            other += 1
+    return agg, other
+
+
+@pytest.mark.parametrize("tile,W,H,K", [(16, 256, 192, 3072), (8, 200, 120, 1500),
+                                        (32, 640, 480, 4800), (16, 333, 97, 2020)])
+def test_grid_ordered_lists_bitexact(tile, W, H, K):
+    """Kernels on a jittered grid (grid order, anisotropic), every 97th made
+    12x wider: most warps take the aggregated walk, the warps holding a wide
+    kernel (and those straddling grid rows) the per-lane one."""
+    t = synth.polygon_image(W, H, 3, 8, K)
+    p = synth.init_params(t, K, 3.0, True, K, aniso=(1.0, 3.0), slope_std=1e-2)
+    chol = p.chol.copy()
+    chol[::97] /= 12.0
+    p = synth.Params(p.mu, chol, p.ea, p.eW)
+    params, r = lists_gpu(p, W, H, 3, tile)
+    off, pk = r.lists()
+    m = model(p, W, H, 3, tile)
+    ref_off, ref_pk = om.bin_tiles(m)
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    agg, other = aggregated_warps(ref_off, ref_pk, K, W, H, tile)
+    assert agg > 0 and other > 0, (agg, other)
+    y, _ = r.render()
+    ref, _, absm = om.render(m, with_scale=True)
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= RTOL_Y * np.maximum(np.abs(ref), absm))
+
+
+def adversarial(seed, W, H, tile, K=160):
+    """Thin and tilted ellipses (aspect up to 60), a < 0 (mirrored factor),
+    very narrow (a up to 40 / px) and nearly flat (a down to 1e-4) kernels,
+    centres on pixel centres, pixel corners and tile corners."""
+    rng = np.random.default_rng(seed)
+    mu = np.empty((K, 2)); chol = np.empty((K, 3))
+    for k in range(K):
+        kind = k % 5
+        if kind == 0:                   # centre on a pixel centre
+            cx, cy = rng.integers(0, W) + 0.5, rng.integers(0, H) + 0.5
+        elif kind == 1:                 # pixel corner
+            cx, cy = float(rng.integers(0, W + 1)), float(rng.integers(0, H + 1))
+        elif kind == 2:                 # tile corner
+            cx = float(tile * rng.integers(0, W // tile + 1))
+            cy = float(tile * rng.integers(0, H // tile + 1))
+        else:
+            cx, cy = rng.uniform(-0.1 * W, 1.1 * W), rng.uniform(-0.1 * H, 1.1 * H)
+        mu[k] = (cx / W, cy / H)
+        s_long = rng.uniform(2.0, 30.0)
+        s_short = s_long / rng.uniform(1.0, 60.0)
+        th = rng.uniform(0, np.pi)
+        R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        L = np.linalg.cholesky(np.linalg.inv(R @ np.diag([s_long ** 2, s_short ** 2]) @ R.T))
+        a, b, c = L[0, 0], L[1, 0], L[1, 1]
+        if k % 7 == 3:
+            a = -a                      # mirrored factor: same |z0| family
+        if k % 11 == 4:
+            a = rng.choice([1e-4, 40.0])
+        chol[k] = (a, b, c)
+    ea = rng.uniform(0, 1, (K, 3))
+    eW = rng.normal(0, 0.05, (K, 3, 2))
+    f = lambda x: x.astype(np.float32)
+    return synth.Params(f(mu), f(chol), f(ea), f(eW))
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_row_masks_exact_on_adversarial_kernels(tile, seed):
+    W, H = 5 * tile + 3, 4 * tile + 5
+    p = adversarial(100 * tile + seed, W, H, tile)
+    params, r = lists_gpu(p, W, H, 3, tile)
+    m = model(p, W, H, 3, tile)
+    off, pk = r.lists()
+    ref_off, ref_pk = om.bin_tiles(m)
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    y, invd = r.render()
+    ref, ref_inv, absm = om.render(m, with_scale=True)
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= RTOL_Y * np.maximum(np.abs(ref), absm)), float(err.max())
+    # the empty-pixel rule and D itself: a dropped kernel changes 1/D
+    gi = invd.cpu().numpy()
+    assert np.array_equal(gi == 0, ref_inv == 0)
+    assert np.all(np.abs(gi - ref_inv) <= RTOL_Y * ref_inv)
+    gy = np.random.default_rng(seed).normal(0, 1, (3, H, W)).astype(np.float32)
+    g = r.backward(params, y, invd, gy=torch.tensor(gy, device="cuda"))
+    ref_g, terms = om.backward(m, gy=gy.astype(np.float64), with_scale=True)
+    for name, a_, b_, t_ in zip(["mu", "chol", "ea", "eW"], g.numpy(), ref_g, terms):
+        b_ = np.asarray(b_, np.float64)
+        den = np.maximum(np.abs(b_), 1e-3 * np.abs(b_).max())
+        den = np.maximum(den, 1e-2 * np.asarray(t_, np.float64))
+        rel = np.abs(np.asarray(a_, np.float64) - b_) / np.where(den > 0, den, 1.0)
+        assert rel.max() <= RTOL_G, f"{name}: {rel.max():.3g}"
