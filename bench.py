@@ -43,6 +43,10 @@ MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measu
 # Kernels launched by one fit step: binning (bbox, scan reduce/top/down,
 # scatter, warp sort, long-list sort), the fused tile kernel, fused Adam.
 KERNELS_PER_STEP = 9
+# The fit re-sorts its kernels spatially every this many steps (FitBatch
+# reorder_every; smoe_fit_reorder, 15 kernels); the timed steps include it.
+REORDER_EVERY = 25
+REORDER_KERNELS = 15
 # From one ncu capture of the fused tile kernel on this workload (profiles/):
 # DRAM bytes per launch and pipe utilisation; valid only while render.cu's
 # code (comments and whitespace aside) is the code that was profiled.
@@ -571,7 +575,7 @@ def main():
     n_phase = min(args.steps, 200)               # eager steps timed phase by phase
     total_iters = args.warmup + 2 * args.steps + n_phase + 5
     fb = FitBatch([tgt], [params], total_iters, lr=synth.PAPER_LR, tile=T, qmax=wl.qmax,
-                  hist=total_iters)
+                  hist=total_iters, reorder_every=REORDER_EVERY)
     desc = api.RasterDesc(W, H, C, T, True, wl.qmax, 1.0)
 
     def pairs_now():
@@ -602,11 +606,14 @@ def main():
             flush.zero_()                       # L2 flush outside the timed region
             ev[s][0].record(stream)
             graph.replay()
+            if (s + 1) % REORDER_EVERY == 0:    # the periodic spatial re-sort, timed with its step
+                fb.reorder()
             ev[s][1].record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     # the same step launched phase by phase (eager), for the breakdown
+    rev = []
     for s in range(n_phase):
         flush.zero_()
         e = pev[s]
@@ -617,6 +624,13 @@ def main():
         e[2].record(stream)
         fb.phase(2)
         e[3].record(stream)
+        if (s + 1) % REORDER_EVERY == 0:
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            r0.record(stream)
+            fb.reorder()
+            r1.record(stream)
+            rev.append((r0, r1))
     torch.cuda.synchronize()
     st = fb.status_code()
     assert st == 0, f"fit status {st}"
@@ -624,6 +638,7 @@ def main():
     tile_ms = [e[1].elapsed_time(e[2]) for e in pev]
     adam_ms = [e[2].elapsed_time(e[3]) for e in pev]
     eager_ms = [e[0].elapsed_time(e[3]) for e in pev]
+    reorder_ms = [a.elapsed_time(b) for a, b in rev]
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
     pairs1, lists1, inrange1 = pairs_now()
     pairs_step = 0.5 * (pairs0 + pairs1)
@@ -661,6 +676,8 @@ def main():
         fb.set_target(0, bufs[cur])
         it = int(args.warmup + 1 + args.steps + n_phase + s)
         fb.launch(1)
+        if (s + 1) % REORDER_EVERY == 0:
+            fb.reorder()
         freed[cur].record(stream)
         host_loss.copy_(fb.loss[0, it:it + 1], non_blocking=True)
     e1.record(stream)
@@ -745,6 +762,7 @@ def main():
                        "l2": "flushed (256 MiB write, untimed) before every timed step",
                        "launch": "one CUDA-graph replay of the whole fit iteration per step "
                                  "(the FitBatch.run(graph_iters=...) path)",
+                       "reorder_every": REORDER_EVERY,
                        "parallelism": f"replicas x{world}",
                        "pairs_per_step": int(pairs_step), "list_pairs": int(lists1),
                        "in_range_pairs_per_step": int(inrange_step)},
@@ -768,6 +786,7 @@ def main():
                          "fraction_of_listed": inrange_step / pairs_step},
             "phases_ms": {"bin": statistics.mean(bin_ms), "fused_tiles": statistics.mean(tile_ms),
                           "adam": statistics.mean(adam_ms), "eager_step": statistics.mean(eager_ms),
+                          "reorder_per_call": statistics.mean(reorder_ms) if reorder_ms else None,
                           "steps": n_phase,
                           "how": "the same step launched phase by phase (no graph), "
                                  "CUDA events between the phases"},
@@ -786,7 +805,8 @@ def main():
                     "launch": "FitBatch.launch(1) per step (no graph: the target buffer "
                               "alternates)",
                     "l2": "not flushed: steps back to back, as a caller runs them"},
-            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "gpu_launches": KERNELS_PER_STEP * args.steps
+                            + REORDER_KERNELS * (args.steps // REORDER_EVERY),
             "clocks": clocks,
         }
         print(json.dumps(out), flush=True)

@@ -262,6 +262,43 @@ SMOE_API smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smo
                                           int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
                                           int32_t *status, void *stream);
 
+/* Spatial reordering of a fit batch's kernels (an aid to the tile binning
+ * of Sec. IV-C, not part of the method).  The fit moves kernel centres, so
+ * after some iterations kernels with consecutive indices are no longer
+ * neighbours and the binning's per-warp aggregation and run merge stop
+ * applying.  This call permutes each image's kernels into tile-major order
+ * of their current centres (centres outside the raster clamp to the nearest
+ * edge tile, non-finite ones go last), ascending current index within a
+ * tile: the parameters and both Adam moments of every group move together,
+ * kernels stay in their image, and the order is a function of the centres
+ * alone.  The model is the same set of kernels; later renders and gradients
+ * differ from those of the unpermuted model only in the order of the FP32
+ * sums over kernels.
+ *   batch, imgs, pair_cap, ws, ws_bytes: as smoe_fit_phase, after
+ *                smoe_fit_init on this workspace; call between iterations
+ *                (the next iteration rebins)
+ *   order        in/out, optional: K_total int32 (device), slot -> the
+ *                kernel's index in the caller's original order, permuted
+ *                with the kernels (initialise to 0 .. K_total-1; slots of
+ *                image b keep values in its own range)
+ *   status       device status word: when it is already set the call
+ *                changes nothing */
+SMOE_API smoe_status smoe_fit_reorder(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                      int64_t pair_cap, void *ws, size_t ws_bytes,
+                                      int32_t *order, int32_t *status, void *stream);
+
+/* Row scatter of a parameter set: dst row (index[i] - base) <- src row i for
+ * i < src->K, in every group (mu 2, chol 3, ea C, eW 2C, logpi 1 values per
+ * row) present in both sets.  Returns a reordered batch's parameters in the
+ * caller's order: src = an image's slots, index = that image's range of the
+ * batch's order array, base = the image's first kernel index.
+ *   index: src->K int32 (device), a permutation of base .. base + K - 1
+ *   dst: K rows (device, not overlapping src)
+ * Returns SMOE_ERR_ARG for a negative K, C not 1 or 3, or missing arrays. */
+SMOE_API smoe_status smoe_scatter_params(const smoe_params *src, const int32_t *index,
+                                         int64_t base, int32_t C, const smoe_params *dst,
+                                         void *stream);
+
 /* Multi-model fusion (Sec. V-C, Eq. 11) of H separate models on any raster:
  * y = (1/H) sum_h y_h, each y_h the render of models[h] on d's W x H raster
  * at d->scale (so a denoised MM-RSMoE result can be resampled at 1-4x), in

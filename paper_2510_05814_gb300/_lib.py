@@ -17,7 +17,7 @@ EXPORTS = ["smoe_version", "smoe_workspace_size", "smoe_bin", "smoe_render",
            "smoe_fit_render_mean", "smoe_render_mean_workspace_size", "smoe_render_mean",
            "smoe_sharpen", "smoe_points_workspace_size",
            "smoe_render_points", "smoe_count_inrange", "smoe_render_static",
-           "smoe_get_status"]
+           "smoe_get_status", "smoe_fit_reorder", "smoe_scatter_params"]
 
 
 class SmoeError(RuntimeError):
@@ -93,6 +93,8 @@ def load():
         "smoe_count_inrange": (I32, [D, I64, P, ctypes.c_size_t, P, P, P, P, P]),
         "smoe_render_static": (I32, [D, PP, P, P, P, P]),
         "smoe_get_status": (I32, [P, P]),
+        "smoe_fit_reorder": (I32, [FB, FI, I64, P, ctypes.c_size_t, P, P, P]),
+        "smoe_scatter_params": (I32, [PP, P, I64, I32, PP, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsmoe.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["bin.cu", "render.cu", "adam.cu", "api.cu", "static_render.cu", "resample.cu"]
+SOURCES = ["bin.cu", "render.cu", "adam.cu", "api.cu", "static_render.cu", "resample.cu",
+           "reorder.cu"]
 # Issue-rate micro-benchmark (the ALU roofline's per-clock peaks), its own library.
 RATES_SRC = "issue_rates.cu"
 RATES_LIB = os.path.join(HERE, "libsmoe_rates.so")

@@ -432,6 +432,29 @@ smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_ima
     return cuda_status(e);
 }
 
+smoe_status smoe_fit_reorder(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                             int64_t pair_cap, void *ws, size_t ws_bytes, int32_t *order,
+                             int32_t *status, void *stream) {
+    Geo g;
+    Bufs w;
+    Layout L;
+    std::vector<ImgDev> tab;
+    smoe_status s = fit_bufs(batch, imgs, pair_cap, ws, ws_bytes, status, &g, &w, &L, &tab);
+    if (s != SMOE_OK) return s;
+    return cuda_status(launch_reorder(g, w, order, static_cast<cudaStream_t>(stream)));
+}
+
+smoe_status smoe_scatter_params(const smoe_params *src, const int32_t *index, int64_t base,
+                                int32_t C, const smoe_params *dst, void *stream) {
+    if (!src || !dst || (C != 1 && C != 3) || src->K < 0 || src->K > 0x7fffffffLL || base < 0)
+        return SMOE_ERR_ARG;
+    if (src->K > 0 && (!index || !src->mu || !src->chol || !src->ea || !dst->mu || !dst->chol ||
+                       !dst->ea))
+        return SMOE_ERR_ARG;
+    return cuda_status(launch_scatter_params(*src, index, base, src->K, C, *dst,
+                                             static_cast<cudaStream_t>(stream)));
+}
+
 smoe_status smoe_sharpen(const float *chol_in, float *chol_out, int64_t K, float factor,
                          void *stream) {
     if (K < 0 || K > 0x7fffffffLL || !(factor > 0.0f) || !std::isfinite(factor) ||

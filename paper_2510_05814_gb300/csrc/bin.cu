@@ -2,15 +2,20 @@
 // per block (Sec. IV-C, Eq. 5) as a counting sort of (tile, kernel) pairs.
 //
 //   k_prep_bbox     one thread per kernel: prepared record, tile rectangle,
-//                   per-tile counts (atomic increments; a large rectangle is
-//                   walked by the whole warp)
+//                   per-tile counts (one atomic per tile of a warp's union box
+//                   when the warp's rectangles are compact, else one per
+//                   covered tile; a large rectangle is walked by the whole warp)
 //   k_scan_*        exclusive prefix sum of the per-tile counts -> tile_off
 //                   (three phases: block sums, scan of the sums, block scans)
-//   k_scatter       one thread per kernel: claim a slot in each covered tile
-//   k_segsort_warp  one warp per tile: restore ascending kernel order (register
-//                   bitonic sort for lists of up to 256 ids)
-//   k_segsort_long  one CTA per longer list (bitonic sort in shared memory up
-//                   to 2048 ids, a bitmap sweep over the kernel-id range above)
+//   k_scatter       one thread per kernel: a slot in each covered tile (claimed
+//                   per union tile for the warp, or one atomic per tile)
+//   k_segsort_warp  one warp per tile: restore ascending kernel order for lists
+//                   of up to 512 ids (register bitonic sorts; from 129 ids on
+//                   first a merge of the ascending per-warp runs the
+//                   aggregated scatter writes)
+//   k_segsort_long  one CTA per longer list (up to 1024 ids the run merge
+//                   first; a bitonic sort in shared memory up to 2048 ids, a
+//                   bitmap sweep over the kernel-id range above)
 //
 // The per-tile lists are the unique sets {k : tile in rect_k} in ascending k,
 // so the output is bit-exact whatever order the atomics took.
@@ -26,7 +31,13 @@ constexpr int kScanChunk = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256;
 constexpr int kSortMax = 2048;                 // bitonic in shared memory up to this
 constexpr int kBitmapWords = 8192;             // 262144 kernel ids per bitmap pass
-constexpr int kLongGrid = 152;                 // CTAs sweeping the queue of long lists (> 1024 ids)
+constexpr int kLongGrid = 152;                 // CTAs sweeping the queue of long lists (> 512 ids)
+constexpr int kBig = 32;                       // rectangles of more tiles are walked by a whole warp
+// The scatter marks the first id of every block it writes contiguously and
+// in ascending order (a warp's covering kernels, or a single id) in the top
+// bit of the 32-bit slot; ids are below 2^31.  The sorts strip it.
+constexpr int32_t kBlockHead = (int32_t)0x80000000u;
+constexpr int32_t kIdMask = 0x7fffffff;
 
 // Add 1 to the count (or claim a slot) of every tile of the rectangles of
 // the warp's kernels.  Small rectangles are walked by their own lane; a large
@@ -34,12 +45,11 @@ constexpr int kLongGrid = 152;                 // CTAs sweeping the queue of lon
 template <bool SCATTER>
 __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect, int64_t t_off,
                                            int tiles_x, int32_t k) {
-    constexpr int kBig = 32;
     const int lane = threadIdx.x & 31;
     const int wdt = rect.z - rect.x + 1;
     const int n = valid && rect.x <= rect.z ? wdt * (rect.w - rect.y + 1) : 0;
     auto visit = [&](int64_t t, int32_t kid) {
-        if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kid;
+        if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kid | kBlockHead;
         else atomicAdd(&w.tile_cnt[t], 1);
     };
     if (n <= kBig) {             // small rectangles: each lane walks its own
@@ -59,7 +69,7 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (slot[u] >= 0) w.pair_tmp[slot[u]] = k;
+                    if (slot[u] >= 0) w.pair_tmp[slot[u]] = k | kBlockHead;
             }
         } else {
             for (int ty = rect.y; n > 0 && ty <= rect.w; ++ty)
@@ -85,24 +95,23 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
 }
 
 // Per-warp aggregation of the walks.  A warp's 32 consecutive kernels are
-// mostly neighbours, so their rectangles overlap: when the union box of the
-// warp's rectangles (one image) holds at most kAggMax tiles and fewer tiles
-// than the rectangles' total, the warp visits each union tile once and adds
-// the number of its kernels covering it with one atomic; the scatter then
-// places the covering kernels at base + their rank in lane order.  Other
-// warps walk lane by lane (walk_rects).  Both passes take the same decision
-// from the same rectangles, so counts and slots agree.
+// mostly neighbours, so their rectangles overlap.  The union box of the
+// warp's small rectangles (at most kBig tiles each) is visited tile by tile:
+// each box tile gets the number of the warp's kernels covering it (large
+// ones included) with one atomic, and the scatter places the covering
+// kernels at base + their rank in lane order, so each warp leaves one
+// ascending block of ids per tile.  The parts of large rectangles outside
+// the box are walked tile by tile by the whole warp.  Warps whose box spans
+// two images, holds more than kAggMax tiles or no fewer tiles than the small
+// rectangles' total walk lane by lane (walk_rects).  Both passes take the
+// same decisions from the same rectangles, so counts and slots agree.
 constexpr int kAggMax = 128;
 constexpr int kBinThreads = 256;
 
 struct WarpAgg {
-    union {
-        int4 rect[32];          // count: the warp's rectangles
-        struct {
-            int base[kAggMax];  // scatter, per union tile: first slot claimed for the warp
-            unsigned bal[kAggMax];   // and the lanes covering it
-        };
-    };
+    int4 rect[32];              // the warp's rectangles
+    int base[kAggMax];          // scatter, per box tile: first slot claimed for the warp
+    unsigned bal[kAggMax];      // and the lanes covering it
 };
 
 template <bool SCATTER>
@@ -116,70 +125,71 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
     const int src = __ffs(any) - 1;
     const int64_t t0 = __shfl_sync(full, t_off, src);
     const bool one_image = __all_sync(full, !has || t_off == t0);
-    const int ux0 = __reduce_min_sync(full, has ? rect.x : 0x7fffffff);
-    const int uy0 = __reduce_min_sync(full, has ? rect.y : 0x7fffffff);
-    const int ux1 = __reduce_max_sync(full, has ? rect.z : -1);
-    const int uy1 = __reduce_max_sync(full, has ? rect.w : -1);
-    const int uw = ux1 - ux0 + 1;
-    const long long nu = (long long)uw * (uy1 - uy0 + 1);
     const int own = has ? (rect.z - rect.x + 1) * (rect.w - rect.y + 1) : 0;
-    const unsigned total = __reduce_add_sync(full, (unsigned)min(own, 1 << 20));
-    if (!one_image || nu > kAggMax || nu >= (long long)total) {
+    const bool small = has && own <= kBig;
+    const int ux0 = __reduce_min_sync(full, small ? rect.x : 0x7fffffff);
+    const int uy0 = __reduce_min_sync(full, small ? rect.y : 0x7fffffff);
+    const int ux1 = __reduce_max_sync(full, small ? rect.z : -1);
+    const int uy1 = __reduce_max_sync(full, small ? rect.w : -1);
+    const int uw = ux1 - ux0 + 1;
+    const long long nu = ux1 >= 0 ? (long long)uw * (uy1 - uy0 + 1) : 0;
+    const unsigned total = __reduce_add_sync(full, small ? (unsigned)own : 0u);
+    if (!one_image || nu == 0 || nu > kAggMax || nu >= (long long)total) {
         walk_rects<SCATTER>(w, valid, rect, t_off, tiles_x, k);
         return;
     }
-    if (!SCATTER) {
-        // count: one union tile per lane, the warp's rectangles from shared memory
-        wa.rect[lane] = has ? rect : make_int4(1, 1, 0, 0);
-        __syncwarp();
-        for (int u = lane; u < (int)nu; u += 32) {
-            const int tx = ux0 + u % uw, ty = uy0 + u / uw;
-            int c = 0;
+    // One box tile per lane: the mask of the warp's lanes covering it (the
+    // rectangles from shared memory); the count adds its popcount, the
+    // scatter claims that many slots and keeps the mask for the ranks.
+    wa.rect[lane] = has ? rect : make_int4(1, 1, 0, 0);
+    __syncwarp();
+    for (int u = lane; u < (int)nu; u += 32) {
+        const int tx = ux0 + u % uw, ty = uy0 + u / uw;
+        unsigned msk = 0;
 #pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
-                const int4 r = wa.rect[l];
-                c += (r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w) ? 1 : 0;
-            }
-            if (c) atomicAdd(&w.tile_cnt[t0 + (int64_t)ty * tiles_x + tx], c);
+        for (int l = 0; l < 32; ++l) {
+            const int4 r = wa.rect[l];
+            msk |= (r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w) ? 1u << l : 0u;
         }
-        __syncwarp();
-        return;
-    }
-    // Scatter: sweep the union box row by row, 32 tiles at a time: one ballot
-    // per tile of the lanes covering it; lane j keeps the ballot of the
-    // chunk's tile j and claims its popcount of slots.
-    const unsigned lower = (1u << lane) - 1u;
-    int u = 0, tx = ux0, ty = uy0;
-    bool row_in = has && rect.y <= ty && ty <= rect.w;
-    while (u < (int)nu) {
-        unsigned mine = 0;
-        int my_tx = 0, my_ty = 0;
-        const int n_chunk = min(32, (int)nu - u);
-        for (int j = 0; j < n_chunk; ++j) {
-            const unsigned bal = __ballot_sync(full, row_in && rect.x <= tx && tx <= rect.z);
-            if (lane == j) { mine = bal; my_tx = tx; my_ty = ty; }
-            if (++tx > ux1) {
-                tx = ux0;
-                ++ty;
-                row_in = has && rect.y <= ty && ty <= rect.w;
-            }
+        const int64_t t = t0 + (int64_t)ty * tiles_x + tx;
+        if (SCATTER) {
+            wa.bal[u] = msk;
+            if (msk) wa.base[u] = atomicAdd(&w.cursor[t], __popc(msk));
+        } else if (msk) {
+            atomicAdd(&w.tile_cnt[t], __popc(msk));
         }
-        if (lane < n_chunk && mine) {
-            const int64_t t = t0 + (int64_t)my_ty * tiles_x + my_tx;
-            wa.base[u + lane] = atomicAdd(&w.cursor[t], __popc(mine));
-            wa.bal[u + lane] = mine;
-        }
-        u += n_chunk;
     }
     __syncwarp();
-    // each lane places its kernel in its own tiles: base + rank in lane order
-    if (has) {
-        for (int y = rect.y; y <= rect.w; ++y) {
+    if (SCATTER && has) {
+        // each lane places its kernel in its tiles inside the box
+        const unsigned lower = (1u << lane) - 1u;
+        const int y0 = max(rect.y, uy0), y1 = min(rect.w, uy1);
+        const int x0 = max(rect.x, ux0), x1 = min(rect.z, ux1);
+        for (int y = y0; y <= y1; ++y) {
             const int ub = (y - uy0) * uw - ux0;
-            for (int x = rect.x; x <= rect.z; ++x) {
+            for (int x = x0; x <= x1; ++x) {
                 const int uu = ub + x;
-                w.pair_tmp[wa.base[uu] + __popc(wa.bal[uu] & lower)] = k;
+                const int rank = __popc(wa.bal[uu] & lower);
+                w.pair_tmp[wa.base[uu] + rank] = rank ? k : (k | kBlockHead);
             }
+        }
+    }
+    // the parts of large rectangles outside the box, one rectangle at a time
+    unsigned big = __ballot_sync(full, has && !small &&
+                                           !(rect.x >= ux0 && rect.z <= ux1 && rect.y >= uy0 &&
+                                             rect.w <= uy1));
+    while (big) {
+        const int bl = __ffs(big) - 1;
+        big &= big - 1;
+        const int4 r = wa.rect[bl];
+        const int32_t kk = __shfl_sync(full, k, bl);
+        const int rw = r.z - r.x + 1, nn = rw * (r.w - r.y + 1);
+        for (int i = lane; i < nn; i += 32) {
+            const int tx = r.x + i % rw, ty = r.y + i / rw;
+            if (tx >= ux0 && tx <= ux1 && ty >= uy0 && ty <= uy1) continue;
+            const int64_t t = t0 + (int64_t)ty * tiles_x + tx;
+            if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kk | kBlockHead;
+            else atomicAdd(&w.tile_cnt[t], 1);
         }
     }
     __syncwarp();
@@ -427,8 +437,8 @@ __device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s
 // Bitonic sort of the warp's 32 E ids in registers, ascending; element
 // p = lane E + i.  Compare-exchange stages whose partner is in another lane
 // (distance j >= E) go through shuffles, the others stay inside the lane.
-template <int E>
-__device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane) {
+template <int E, typename V>
+__device__ __forceinline__ void warp_bitonic(V (&v)[E], int lane) {
     constexpr int P = 32 * E;
 #pragma unroll
     for (int k = 2; k <= P; k <<= 1) {
@@ -440,7 +450,7 @@ __device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane) {
 #pragma unroll
                 for (int i = 0; i < E; ++i) {
                     const bool up = ((lane * E + i) & k) == 0;
-                    const int o = __shfl_xor_sync(0xffffffffu, v[i], lj);
+                    const V o = __shfl_xor_sync(0xffffffffu, v[i], lj);
                     v[i] = (lower == up) ? min(v[i], o) : max(v[i], o);
                 }
             } else {
@@ -449,7 +459,7 @@ __device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane) {
                     const int ip = i ^ j;
                     if (ip > i) {
                         const bool up = ((lane * E + i) & k) == 0;
-                        const int a = v[i], b = v[ip];
+                        const V a = v[i], b = v[ip];
                         v[i] = up ? min(a, b) : max(a, b);
                         v[ip] = up ? max(a, b) : min(a, b);
                     }
@@ -465,9 +475,9 @@ __device__ __forceinline__ void warp_sort_list(const Bufs &w, int64_t start, int
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int p = lane * E + i;
-        v[i] = p < n ? w.pair_tmp[start + p] : 0x7fffffff;
+        v[i] = p < n ? w.pair_tmp[start + p] & kIdMask : 0x7fffffff;
     }
-    warp_bitonic<E>(v, lane);
+    warp_bitonic<E, int>(v, lane);
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int p = lane * E + i;
@@ -475,11 +485,134 @@ __device__ __forceinline__ void warp_sort_list(const Bufs &w, int64_t start, int
     }
 }
 
-// One warp per tile: lists of up to kWarpSortMax ids are sorted in registers
-// (8, 16 or 32 per lane); longer lists are queued for k_segsort_long.
-constexpr int kWarpSortMax = 1024;
+// The scatter writes each list as blocks, each marked at its first id and
+// ascending (a warp's covering kernels, or a single id), placed in any order.
+// When every block is ascending, there are at most kMaxRuns of them and,
+// ordered by their first ids, each starts above the end of the one before,
+// the sorted list is the blocks in that order: sort the first ids (two per
+// lane), scan the block lengths, move each id.  Returns false, having
+// written nothing, when the list is not of that form (the caller sorts it in
+// full).  E ids per lane: n <= 32 E.
+constexpr int kMaxRuns = 64;
 
-__global__ void __launch_bounds__(256) k_segsort_warp(int64_t n_tiles, Bufs w) {
+struct WarpRuns {
+    int start[kMaxRuns + 1], dest[kMaxRuns];
+    int first[kMaxRuns], last[kMaxRuns];
+};
+
+template <int E>
+__device__ __forceinline__ bool warp_merge_runs(const Bufs &w, int64_t start, int n, int lane,
+                                                WarpRuns &sr) {
+    const unsigned full = 0xffffffffu;
+    int v[E];
+    unsigned hmask = 0;                                // bit i: element i opens a block
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        const int raw = p < n ? w.pair_tmp[start + p] : kIdMask;
+        v[i] = raw & kIdMask;
+        if (p < n && (raw < 0 || p == 0)) hmask |= 1u << i;
+    }
+    const int prev_last = __shfl_up_sync(full, v[E - 1], 1);
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        if (p < n && !((hmask >> i) & 1u) && v[i] <= (i ? v[i - 1] : prev_last)) ok = false;
+    }
+    if (!__all_sync(full, ok)) return false;
+    const int hc = __popc(hmask);
+    int incl = hc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int R = __shfl_sync(full, incl, 31);
+    if (R > kMaxRuns) return false;
+    // block starts, first and last ids (an element ends its block when the
+    // next one opens a block or the list ends)
+    const unsigned next_first = __shfl_down_sync(full, hmask & 1u, 1);
+    int r = incl - hc;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        if ((hmask >> i) & 1u) {
+            sr.start[r] = p;
+            sr.first[r] = v[i];
+            ++r;
+        }
+        const bool ends = p == n - 1 ||
+                          (i + 1 < E ? ((hmask >> (i + 1)) & 1u) != 0 : (lane < 31 && next_first));
+        if (p < n && ends) sr.last[r - 1] = v[i];
+    }
+    if (lane == 0) sr.start[R] = n;
+    __syncwarp();
+    // blocks by first id: first << 32 | block, two per lane
+    constexpr int KE = kMaxRuns / 32;
+    unsigned long long x[KE];
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const int b = KE * lane + e;
+        x[e] = b < R ? ((unsigned long long)(unsigned)sr.first[b] << 32) | (unsigned)b : ~0ull;
+    }
+    warp_bitonic<KE, unsigned long long>(x, lane);
+    // each block starts above the end of the block before it
+    const unsigned long long prev = __shfl_up_sync(full, x[KE - 1], 1);
+    bool disjoint = true;
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const int q = KE * lane + e;
+        const unsigned long long pq = e ? x[e - 1] : prev;
+        if (q > 0 && q < R &&
+            (int)(x[e] >> 32) <= sr.last[(int)(pq & 0xffffffffull)])
+            disjoint = false;
+    }
+    if (!__all_sync(full, disjoint)) return false;
+    int len[KE], d = 0;
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const int q = KE * lane + e;
+        const int bi = (int)(x[e] & 0xffffffffull);
+        len[e] = q < R ? sr.start[bi + 1] - sr.start[bi] : 0;
+        d += len[e];
+    }
+    int incl_d = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl_d, o);
+        if (lane >= o) incl_d += y;
+    }
+    int at = incl_d - d;
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < KE; ++e) {
+        const int q = KE * lane + e;
+        if (q < R) sr.dest[x[e] & 0xffffffffull] = at;
+        at += len[e];
+    }
+    __syncwarp();
+    int rb = incl - hc - 1;                            // block of the elements before my first head
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int p = lane * E + i;
+        if (p < n) {
+            if ((hmask >> i) & 1u) ++rb;
+            w.pair_k[start + sr.dest[rb] + (p - sr.start[rb])] = v[i];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// One warp per tile: lists of up to 512 ids are sorted in registers (a
+// bitonic sort of the smallest power of two >= 32 that holds the list, 1 to
+// 16 ids per lane; from 129 ids on the run merge first); longer ones are
+// queued for k_segsort_long.
+constexpr int kShortSortThreads = 128;
+
+__global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(int64_t n_tiles, Bufs w) {
+    __shared__ WarpRuns runs[kShortSortThreads / 32];
     if (status_bad(w.status)) return;
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -487,15 +620,21 @@ __global__ void __launch_bounds__(256) k_segsort_warp(int64_t n_tiles, Bufs w) {
     const int64_t start = w.tile_off[t];
     const int n = (int)(w.tile_off[t + 1] - start);
     if (n <= 1) {
-        if (n == 1 && lane == 0) w.pair_k[start] = w.pair_tmp[start];
+        if (n == 1 && lane == 0) w.pair_k[start] = w.pair_tmp[start] & kIdMask;
         return;
     }
-    if (n <= 256) {
-        warp_sort_list<8>(w, start, n, lane);
+    if (n <= 32) {
+        warp_sort_list<1>(w, start, n, lane);
+    } else if (n <= 64) {
+        warp_sort_list<2>(w, start, n, lane);
+    } else if (n <= 128) {
+        warp_sort_list<4>(w, start, n, lane);
+    } else if (n <= 256) {
+        if (!warp_merge_runs<8>(w, start, n, lane, runs[threadIdx.x >> 5]))
+            warp_sort_list<8>(w, start, n, lane);
     } else if (n <= 512) {
-        warp_sort_list<16>(w, start, n, lane);
-    } else if (n <= kWarpSortMax) {
-        warp_sort_list<32>(w, start, n, lane);
+        if (!warp_merge_runs<16>(w, start, n, lane, runs[threadIdx.x >> 5]))
+            warp_sort_list<16>(w, start, n, lane);
     } else if (lane == 0) {
         w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
     }
@@ -506,10 +645,30 @@ __global__ void __launch_bounds__(kSortThreads) k_segsort_long(const __grid_cons
                                                                Bufs w) {
     if (status_bad(w.status)) return;
     __shared__ uint32_t s[kBitmapWords];
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ WarpRuns runs[kWarps];
+    __shared__ bool merged[kWarps];
     const int n_long = *w.n_long;
-    for (int q = blockIdx.x; q < n_long; q += gridDim.x) {
-        segsort_tile(g, w, w.long_q[q], s);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this CTA's lists are q = blockIdx.x + j gridDim.x; kWarps at a time its
+    // warps try the run merge (up to 1024 ids), then the CTA sorts the rest
+    for (int q0 = blockIdx.x; q0 < n_long; q0 += gridDim.x * kWarps) {
+        const int q = q0 + warp * gridDim.x;
+        bool ok = false;
+        if (q < n_long) {
+            const int64_t t = w.long_q[q];
+            const int64_t start = w.tile_off[t];
+            const int n = (int)(w.tile_off[t + 1] - start);
+            ok = n <= 1024 && warp_merge_runs<32>(w, start, n, lane, runs[warp]);
+        }
+        if (lane == 0) merged[warp] = ok;
         __syncthreads();
+        for (int j = 0; j < kWarps; ++j) {
+            const int qq = q0 + j * gridDim.x;
+            if (qq >= n_long) break;
+            if (!merged[j]) segsort_tile(g, w, w.long_q[qq], s);
+            __syncthreads();
+        }
     }
 }
 
@@ -523,7 +682,7 @@ __device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s
         while (P < n) P <<= 1;
         int *v = reinterpret_cast<int *>(s);
         for (int i = tid; i < P; i += kSortThreads)
-            v[i] = i < n ? w.pair_tmp[start + i] : 0x7fffffff;
+            v[i] = i < n ? w.pair_tmp[start + i] & kIdMask : 0x7fffffff;
         __syncthreads();
         for (int k = 2; k <= P; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
@@ -549,7 +708,7 @@ __device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s
         for (int i = tid; i < kBitmapWords; i += kSortThreads) s[i] = 0u;
         __syncthreads();
         for (int i = tid; i < n; i += kSortThreads) {
-            const int64_t d = (int64_t)w.pair_tmp[start + i] - w0;
+            const int64_t d = (int64_t)(w.pair_tmp[start + i] & kIdMask) - w0;
             if (d >= 0 && d < win) atomicOr(&s[d >> 5], 1u << (d & 31));
         }
         __syncthreads();
@@ -591,8 +750,14 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
         const unsigned gb = (unsigned)((g.K_total + kBinThreads - 1) / kBinThreads);
         k_scatter<<<gb, kBinThreads, 0, st>>>(g, w);
     }
+    return launch_sort_lists(g, w, st);
+}
+
+cudaError_t launch_sort_lists(const Geo &g, const Bufs &w, cudaStream_t st) {
+    const int64_t n = g.tiles_total;
     if (n > 0) {
-        k_segsort_warp<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, w);
+        constexpr int wpb = kShortSortThreads / 32;
+        k_segsort_warp<<<(unsigned)((n + wpb - 1) / wpb), kShortSortThreads, 0, st>>>(n, w);
         const int64_t gl = n < kLongGrid ? n : kLongGrid;
         k_segsort_long<<<(unsigned)gl, kSortThreads, 0, st>>>(g, w);
     }

@@ -157,6 +157,14 @@ __device__ __forceinline__ bool status_bad(const int32_t *status) {
 // launchers (host side, no synchronisation)
 // --------------------------------------------------------------------------
 cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st);
+// Sort every tile's segment pair_tmp[tile_off[t] .. tile_off[t+1]) into
+// pair_k in ascending order (the last step of launch_bin).
+cudaError_t launch_sort_lists(const Geo &g, const Bufs &w, cudaStream_t st);
+// Spatial reordering of a fit batch's kernels (see smoe_fit_reorder).
+cudaError_t launch_reorder(const Geo &g, const Bufs &w, int32_t *order, cudaStream_t st);
+// dst row index[i] - base <- src row i, for every group present in both sets.
+cudaError_t launch_scatter_params(const smoe_params &src, const int32_t *index, int64_t base,
+                                  int64_t K, int C, const smoe_params &dst, cudaStream_t st);
 cudaError_t launch_render(const Geo &g, const Bufs &w, float *y, float *inv_d,
                           cudaStream_t st);
 // Exclusive prefix sum of n counters into off[0..n] (off[n] = min(total, cap),

@@ -25,12 +25,17 @@ class FitBatch:
     rbf: fit the unnormalised RBF sum of Eq. 1 instead of the softmax gates;
     persistent: run the fused tile kernel as one persistent grid;
     deterministic: per-pair gradient partials added in a fixed order (a fit
-    is then bit-reproducible and independent of the rest of the batch)."""
+    is then bit-reproducible and independent of the rest of the batch);
+    reorder_every: in run(), re-sort each image's kernels into tile-major
+    order of their centres every that many iterations (smoe_fit_reorder: the
+    fit moves the centres and the binning is faster when consecutive kernels
+    are neighbours).  The batch's parameter tensors then hold the kernels in
+    that order; params_of() returns them in the caller's order."""
 
     def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
                  qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
                  persistent=False, pair_cap=None, moments=None, steps=None,
-                 deterministic=False, device="cuda", rbf=False):
+                 deterministic=False, device="cuda", rbf=False, reorder_every=None):
         """moments: optional list of (m, v) SMoEParams per image and steps an
         optional list of iterations already done: a run that continues in a
         re-formed batch keeps its Adam state and schedule position."""
@@ -58,6 +63,13 @@ class FitBatch:
         self.step = torch.tensor(list(steps) if steps is not None else [0] * self.B,
                                  dtype=torch.int32, device=device)
         self._continue = moments is not None
+        self.reorder_every = int(reorder_every) if reorder_every else None
+        self.k_off = [int(x) for x in np.concatenate([[0], np.cumsum(self.Ks)[:-1]])]
+        # slot -> kernel index in the caller's order (global over the batch)
+        self.order = (torch.arange(sum(self.Ks), dtype=torch.int32, device=device)
+                      if self.reorder_every else None)
+        self._since_reorder = 0
+        self._reorder_graph = None
         self.hist = int(hist if hist is not None else max(self.iters))
         self.loss = torch.zeros(self.B, max(self.hist, 1), dtype=torch.float64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
@@ -105,9 +117,45 @@ class FitBatch:
                                 _ptr(self.ws), self.ws.numel(), int(reset), _ptr(self.status),
                                 _stream(None)), "smoe_fit_init")
         self.graph = None
+        self._reorder_graph = None
 
     def params_of(self, b):
-        return self.params[b]
+        """Image b's parameters in the caller's kernel order: the batch's own
+        tensors, or (after reordering) a copy scattered back through the
+        order map by smoe_scatter_params."""
+        if self.order is None:
+            return self.params[b]
+        src = self.params[b]
+        dst = src.zeros_like()
+        if src.K:
+            idx = self.order[self.k_off[b]:self.k_off[b] + src.K]
+            check(_lib.load().smoe_scatter_params(ctypes.byref(src.c()), _ptr(idx), self.k_off[b],
+                                                  self.C, ctypes.byref(dst.c()), _stream(None)),
+                  "smoe_scatter_params")
+        return dst
+
+    def _reorder_call(self, stream=None):
+        check(_lib.load().smoe_fit_reorder(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                           _ptr(self.ws), self.ws.numel(),
+                                           _ptr(self.order) if self.order is not None else None,
+                                           _ptr(self.status), _stream(stream)),
+              "smoe_fit_reorder")
+
+    def reorder(self, stream=None):
+        """Re-sort every image's kernels into tile-major order of their centres
+        (smoe_fit_reorder); parameters and Adam moments move together.  On
+        the current stream it replays a captured CUDA graph of the call (its
+        launches are many and short)."""
+        if stream is not None:
+            self._reorder_call(stream)
+        else:
+            if self._reorder_graph is None:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    self._reorder_call()
+                self._reorder_graph = g
+            self._reorder_graph.replay()
+        self._since_reorder = 0
 
     def set_target(self, b, target):
         """Point image b at another target tensor of the same shape (for
@@ -160,6 +208,8 @@ class FitBatch:
         check_every = check_every or n_iters
         while done < n_iters:
             chunk = min(check_every, n_iters - done)
+            if self.reorder_every:
+                chunk = min(chunk, self.reorder_every - self._since_reorder)
             before = self.step.clone()
             if graph_iters:
                 if self.graph is None or self.graph_iters != graph_iters:
@@ -179,10 +229,16 @@ class FitBatch:
                 self._setup(reset=False)
                 progressed = int((self.step - before).max().item())
                 done += progressed
+                if self.reorder_every:
+                    self._since_reorder += progressed
                 continue
             if st != _lib.SMOE_OK:
                 raise SmoeError(st, "smoe_fit")
             done += chunk
+            if self.reorder_every:
+                self._since_reorder += chunk
+                if self._since_reorder >= self.reorder_every:
+                    self.reorder()
         return self
 
     def render_mean(self, out=None, stream=None):

@@ -242,9 +242,9 @@ def test_kernels_on_tile_edges(tile):
 
 @pytest.mark.parametrize("K", [400, 700, 1500])
 def test_mid_length_lists_are_bitexact(K):
-    """Lists of 257-512 and 513-1024 ids take the warp register sorts with
-    16 and 32 ids per lane, longer ones the shared-memory sort: the lists
-    are still bit-exact and the render matches."""
+    """Lists of 257-512 ids take the warp register sort with 16 ids per
+    lane, longer ones the shared-memory sort: the lists are still bit-exact
+    and the render matches."""
     p = rand_case(40 + K, 48, 48, 3, K, True, sig=(20.0, 30.0), span=(0.2, 0.8))
     params, r = gpu_raster(p, 48, 48, 3, 16, 1.0)
     off, pk = r.lists()
