@@ -20,11 +20,14 @@ struct AdamK {
     float inv_sqrt_bc2;    // 1 / sqrt(1 - b2^t)
 };
 
+// Every operation rounded explicitly: the update is the same bit for bit in
+// every kernel and code path that inlines it (no contraction left to the
+// compiler), so a fit does not depend on how its kernels share CTAs.
 __device__ __forceinline__ void adam1(float &p, float g, float &m, float &v, const AdamK &k) {
-    m = fmaf(k.be.omb1, g - m, m);
-    v = fmaf(k.be.b2, v, k.be.omb2 * g * g);
-    const float denom = sqrtf(v) * k.inv_sqrt_bc2 + k.be.eps;
-    p -= k.step_size * (m / denom);
+    m = __fmaf_rn(k.be.omb1, __fsub_rn(g, m), m);
+    v = __fmaf_rn(k.be.b2, v, __fmul_rn(__fmul_rn(k.be.omb2, g), g));
+    const float denom = __fmaf_rn(__fsqrt_rn(v), k.inv_sqrt_bc2, k.be.eps);
+    p = __fmaf_rn(-k.step_size, __fdiv_rn(m, denom), p);
 }
 
 // One launch over the groups of a SoA parameter set; zeroes g.

@@ -123,7 +123,10 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
     const unsigned any = __ballot_sync(full, has);
     if (!any) return;
     const int src = __ffs(any) - 1;
+    // the image of the warp's kernels with a rectangle: every lane, also one
+    // of another image whose rectangle is empty, indexes that image's tiles
     const int64_t t0 = __shfl_sync(full, t_off, src);
+    const int tx_n = __shfl_sync(full, tiles_x, src);
     const bool one_image = __all_sync(full, !has || t_off == t0);
     const int own = has ? (rect.z - rect.x + 1) * (rect.w - rect.y + 1) : 0;
     const bool small = has && own <= kBig;
@@ -151,7 +154,7 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
             const int4 r = wa.rect[l];
             msk |= (r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w) ? 1u << l : 0u;
         }
-        const int64_t t = t0 + (int64_t)ty * tiles_x + tx;
+        const int64_t t = t0 + (int64_t)ty * tx_n + tx;
         if (SCATTER) {
             wa.bal[u] = msk;
             if (msk) wa.base[u] = atomicAdd(&w.cursor[t], __popc(msk));
@@ -187,7 +190,7 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
         for (int i = lane; i < nn; i += 32) {
             const int tx = r.x + i % rw, ty = r.y + i / rw;
             if (tx >= ux0 && tx <= ux1 && ty >= uy0 && ty <= uy1) continue;
-            const int64_t t = t0 + (int64_t)ty * tiles_x + tx;
+            const int64_t t = t0 + (int64_t)ty * tx_n + tx;
             if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kk | kBlockHead;
             else atomicAdd(&w.tile_cnt[t], 1);
         }

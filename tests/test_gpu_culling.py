@@ -157,3 +157,31 @@ def test_row_masks_exact_on_adversarial_kernels(tile, seed):
         den = np.maximum(den, 1e-2 * np.asarray(t_, np.float64))
         rel = np.abs(np.asarray(a_, np.float64) - b_) / np.where(den > 0, den, 1.0)
         assert rel.max() <= RTOL_G, f"{name}: {rel.max():.3g}"
+
+
+def test_batch_warps_straddling_images_with_offimage_kernels():
+    """A warp holding the last kernels of one image, moved off its raster
+    (empty rectangles), and the first kernels of the next image (another
+    width): the batched fit bins and steps every image exactly as a fit of
+    that image alone (deterministic accumulation: bit for bit)."""
+    from paper_2510_05814_gb300.fit import FitBatch
+    shapes = [(70, 50, 40), (120, 40, 70), (50, 90, 45)]
+    ts, ps = [], []
+    for i, (W, H, K) in enumerate(shapes):
+        t = synth.polygon_image(W, H, 3, 5, 80 + i)
+        p = synth.init_params(t, K, 4.0, True, 80 + i)
+        mu = p.mu.copy()
+        mu[-9:] = (3.0, -2.0)                 # off the raster: empty rectangles
+        ts.append(torch.tensor(t, device="cuda"))
+        ps.append(synth.Params(mu, p.chol, p.ea, p.eW))
+    lr = (1e-2, 1e-3, 1e-2, 1e-2, 1e-2)
+    fb = FitBatch(ts, [api.SMoEParams.from_numpy(p) for p in ps], 3, lr=lr, tile=8,
+                  deterministic=True)
+    fb.run(3)
+    for b in range(len(shapes)):
+        one = FitBatch([ts[b]], [api.SMoEParams.from_numpy(ps[b])], 3, lr=lr, tile=8,
+                       deterministic=True)
+        one.run(3)
+        np.testing.assert_allclose(fb.losses()[b, :3], one.losses()[0, :3], rtol=1e-12)
+        for x, y in zip(fb.params_of(b).tensors(), one.params_of(0).tensors()):
+            assert torch.equal(x, y)
