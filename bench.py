@@ -40,6 +40,7 @@ WORKLOAD = ("rgb2048_K262144_linear_aniso: 2048x2048 RGB fp32, 40 ramp polygons 
             "texture 0.1, K=262144 anisotropic kernels (area sigma 5 px, aspect 1-3), linear "
             "experts, 16x16 tiles, q_max 9, Adam at the paper's rates")
 MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measurement fails
+FP32_OPS_PER_PAIR = 67            # algorithmic FP32 lane ops per fwd+bwd pair, RGB linear
 # Kernels launched by one fit step: binning (bbox, scan reduce/top/down,
 # scatter, warp sort, long-list sort), the fused tile kernel, fused Adam.
 KERNELS_PER_STEP = 9
@@ -745,6 +746,13 @@ def main():
     ex2_peak = mufu * sms * sm_load * 1e6                          # ex2 / s
     tile_s = statistics.mean(tile_ms) / 1e3
     ex2_achieved = 2.0 * pairs_step / tile_s                       # fwd + bwd: 2 ex2 / pair
+    # FP32 roofline on the pairs that contribute (q <= q_max): the algorithmic
+    # FP32 lane operations of one fwd+bwd pair, RGB linear, against the
+    # measured FFMA lane rate (listed pairs would exceed 1: culled pairs cost
+    # the kernel next to nothing)
+    ffma = rates["ffma"] if rates else 128.0
+    fma_peak = ffma * sms * sm_load * 1e6
+    fma_achieved = FP32_OPS_PER_PAIR * inrange_step / tile_s
     ncu = None
     if NCU["render_cu_code_sha256"] and NCU["render_cu_code_sha256"] == code_sha256(
             os.path.join(ROOT, "paper_2510_05814_gb300", "csrc", "render.cu")):
@@ -791,6 +799,14 @@ def main():
                              "fma_pipe_active": ncu["fma_pipe_active"],
                              "issue_active": ncu["issue_active"],
                              "xu_active": ncu["xu_active"]}},
+            "roofline_fma": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
+                             "achieved": fma_achieved / 1e12, "peak": fma_peak / 1e12,
+                             "unit": "T FP32 lane-ops/s", "frac": fma_achieved / fma_peak,
+                             "basis": (f"{FP32_OPS_PER_PAIR} FP32 lane operations per in-range "
+                                       "fwd+bwd pair (19 forward + 48 backward, RGB linear) x "
+                                       "in-range pairs / fused-kernel time; peak "
+                                       f"{ffma:.1f} FFMA lanes/clk/SM x {sms} SMs x "
+                                       f"{sm_load:.0f} MHz")},
             "value_fwd_bwd_only": pairs_step / tile_s / 1e9,
             # pairs with q <= q_max (the ones that contribute) per second of the
             # fused tile kernel, and their share of the listed pairs

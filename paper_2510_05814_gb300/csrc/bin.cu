@@ -89,8 +89,25 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
         const int tx_n = __shfl_sync(0xffffffffu, tiles_x, src);
         const int32_t kk = __shfl_sync(0xffffffffu, k, src);
         const int rw = r.z - r.x + 1, nn = rw * (r.w - r.y + 1);
-        for (int i = lane; i < nn; i += 32)
-            visit(to + (int64_t)(r.y + i / rw) * tx_n + r.x + i % rw, kk);
+        if (SCATTER) {
+            // four slot claims in flight per lane before their stores
+            for (int i0 = lane; i0 < nn; i0 += 128) {
+                int slot[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + 32 * u;
+                    slot[u] = i < nn ? atomicAdd(&w.cursor[to + (int64_t)(r.y + i / rw) * tx_n +
+                                                           r.x + i % rw], 1)
+                                     : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (slot[u] >= 0) w.pair_tmp[slot[u]] = kk | kBlockHead;
+            }
+        } else {
+            for (int i = lane; i < nn; i += 32)
+                visit(to + (int64_t)(r.y + i / rw) * tx_n + r.x + i % rw, kk);
+        }
     }
 }
 
@@ -187,12 +204,25 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
         const int4 r = wa.rect[bl];
         const int32_t kk = __shfl_sync(full, k, bl);
         const int rw = r.z - r.x + 1, nn = rw * (r.w - r.y + 1);
-        for (int i = lane; i < nn; i += 32) {
-            const int tx = r.x + i % rw, ty = r.y + i / rw;
-            if (tx >= ux0 && tx <= ux1 && ty >= uy0 && ty <= uy1) continue;
-            const int64_t t = t0 + (int64_t)ty * tx_n + tx;
-            if (SCATTER) w.pair_tmp[atomicAdd(&w.cursor[t], 1)] = kk | kBlockHead;
-            else atomicAdd(&w.tile_cnt[t], 1);
+        // four tiles per lane at a time: the scatter's slot claims in flight
+        // before their stores
+        for (int i0 = lane; i0 < nn; i0 += 128) {
+            int slot[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + 32 * u;
+                slot[u] = -1;
+                if (i >= nn) continue;
+                const int tx = r.x + i % rw, ty = r.y + i / rw;
+                if (tx >= ux0 && tx <= ux1 && ty >= uy0 && ty <= uy1) continue;
+                const int64_t t = t0 + (int64_t)ty * tx_n + tx;
+                if (SCATTER) slot[u] = atomicAdd(&w.cursor[t], 1);
+                else atomicAdd(&w.tile_cnt[t], 1);
+            }
+            if (SCATTER)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (slot[u] >= 0) w.pair_tmp[slot[u]] = kk | kBlockHead;
         }
     }
     __syncwarp();
