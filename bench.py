@@ -40,7 +40,12 @@ WORKLOAD = ("rgb2048_K262144_linear_aniso: 2048x2048 RGB fp32, 40 ramp polygons 
             "texture 0.1, K=262144 anisotropic kernels (area sigma 5 px, aspect 1-3), linear "
             "experts, 16x16 tiles, q_max 9, Adam at the paper's rates")
 MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measurement fails
-FP32_OPS_PER_PAIR = 67            # algorithmic FP32 lane ops per fwd+bwd pair, RGB linear
+# Algorithmic FP32 lane operations per in-range fwd+bwd pair, RGB linear
+# experts: 19 in the forward and 48 in the backward (the per-pair count of the
+# method's formulas, Eqs. 2-5 and their chain rule).
+FP32_OPS_PER_PAIR = 67
+# PSNR the fit-to-PSNR leg times the 2048^2 fit to.
+FIT_TARGET_DB = 50.0
 # Kernels launched by one fit step: binning (bbox, scan reduce/top/down,
 # scatter, warp sort, long-list sort), the fused tile kernel, fused Adam.
 KERNELS_PER_STEP = 9
@@ -49,12 +54,13 @@ KERNELS_PER_STEP = 9
 REORDER_EVERY = 25
 REORDER_KERNELS = 15
 # From one ncu capture of the fused tile kernel on this workload (profiles/):
-# DRAM bytes per launch and pipe utilisation; valid only while render.cu's
-# code (comments and whitespace aside) is the code that was profiled.
+# DRAM bytes per launch, pipe utilisation and the executed FP32 lane
+# operations (FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) thread
+# instructions); valid only while render.cu's code (comments and whitespace
+# aside) is the code that was profiled.
 NCU = {"render_cu_code_sha256": "023a846244615376ce0e0d757481649c77f809707901515cfd6718cc83e15ca3",
-       "bytes_per_launch": 105.25824e6, "fma_pipe_active": 0.610, "issue_active": 0.600,
-       "xu_active": 0.129}
-
+       "bytes_per_launch": 103.523072e6, "fma_pipe_active": 0.624, "issue_active": 0.613,
+       "xu_active": 0.129, "fp32_lane_ops": 15.535109205e9}
 
 def issue_rates():
     """Measured lane operations per clock per SM of ex2 / FFMA / packed
@@ -275,7 +281,7 @@ def run_batched(args):
         t = synth.polygon_image(W, H, 3, 40, 400 + i, texture_amp=0.1)
         targets.append(torch.tensor(t, device="cuda"))
         params.append(api.SMoEParams.from_numpy(synth.init_params(t, (W * H) // 16, 5.0, True, 400 + i)))
-    lr = synth.PAPER_LR
+    lr = [synth.fit_rates(W, H) for W, H in sizes]
     tr = autotune.tune(targets, params, lr, tiles=(8, 16, 32), persistent=(False, True))
     n = args.iters
     # batched: graph of `chunk` iterations replayed
@@ -377,7 +383,7 @@ def run_denoise(args):
         tn = torch.tensor(noisy, device="cuda")
         for nm in args.models:
             models = denoise.init_models(noisy, nm, K, 5.0, True, seed=500)
-            fb = FitBatch([tn] * nm, models, n, lr=synth.PAPER_LR, tile=16)
+            fb = FitBatch([tn] * nm, models, n, lr=synth.fit_rates(W, H), tile=16)
             fb.capture(chunk)
             torch.cuda.synchronize()
             e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -398,7 +404,7 @@ def run_denoise(args):
         "metric": "MM-RSMoE denoising: PSNR of the fused image and GPU time of H fits + fusion",
         "mode": "denoise", "image": f"{W}x{H}x3 synthetic (30 ramp polygons + Perlin 0.1, "
                                     f"clipped to [0,1]) + N(0, var) noise",
-        "kernels_per_model": K, "iters": n, "lr": list(synth.PAPER_LR), "tile": 16,
+        "kernels_per_model": K, "iters": n, "lr": list(synth.fit_rates(W, H)), "tile": 16,
         "rows": rows, "data": "synthetic", "dtype": "f32",
     }), flush=True)
 
@@ -406,8 +412,8 @@ def run_denoise(args):
 def run_quality(args):
     """Fit quality and speed on the paper-shaped workloads: the 128x128 grey
     image (K = 256, constant experts, 100 iterations at lr 1e-2) and the
-    512x512 RGB image (K = 16384, linear experts, 2000 iterations at the
-    paper's rates) as softmax-gated R-SMoE (Eq. 4) and with learned gate
+    512x512 RGB image (K = 16384, linear experts, 2000 and 10000 iterations
+    at the paper's rates) as softmax-gated R-SMoE (Eq. 4) and with learned gate
     weights pi_k; then softmax gates against the unnormalised RBF sum of
     Eq. 1 (the Gaussian-splatting regression the paper compares against)
     with constant experts at equal kernel counts.  PSNR against the target; iterations/s from CUDA events
@@ -450,28 +456,28 @@ def run_quality(args):
 
     rows = []
     g = synth.plain_gray_128()
-    rows.append(one("config 1: grey 128^2", g.target, g.params, 100, (1e-2,) * 5))
+    # workload 1 gives one rate, 1e-2, for every group; its centre rate is
+    # read in pixels like the paper's (synth.fit_rates)
+    lr1 = (1e-2 / 128, 1e-2 / 128, 1e-2, 1e-2, 1e-2)
+    rows.append(one("config 1: grey 128^2", g.target, g.params, 100, lr1))
     c2 = synth.rgb_512()
-    lr_pi = tuple(synth.PAPER_LR) + (1e-2,)
-    rows.append(one("config 2: RGB 512^2", c2.target, c2.params, 2000, synth.PAPER_LR))
-    rows.append(one("config 2, learned pi", c2.target, c2.params, 2000, lr_pi, pi=True))
+    lr2 = synth.fit_rates(512, 512)
+    rows.append(one("config 2: RGB 512^2", c2.target, c2.params, 2000, lr2))
+    rows.append(one("config 2, learned pi", c2.target, c2.params, 2000,
+                    synth.fit_rates(512, 512, lr_pi=1e-2), pi=True))
+    rows.append(one("config 2, 10000 iterations", c2.target, c2.params, 10000, lr2))
     # Sparsity comparison of Sec. II / VII: constant experts (the colours of a
     # Gaussian-splatting model), softmax gates against the RBF sum at equal
-    # kernel counts, the paper's protocol of 10000 Adam iterations.  The RBF
-    # colours start at target x spacing^2 / (2 pi sigma^2), the inverse of the
-    # kernels' mean overlap on the grid, so that both start near the target.
-    # The rates: the paper's, and ten times its L / expert rates with a tenth
-    # of its centre rate (under the per-pixel cutoff, pixels that no kernel
-    # reaches get y = 0 and no gradient; the faster shape rates leave fewer).
-    fast = (1e-3, 1e-6, 1e-2, 1e-2, 1e-2)
+    # kernel counts, the paper's protocol of 10000 Adam iterations at its
+    # rates.  The RBF colours start at target x spacing^2 / (2 pi sigma^2),
+    # the inverse of the kernels' mean overlap on the grid, so that both
+    # start near the target.
     for K in (4096, 16384):
         pk = synth.init_params(c2.target, K, 5.0, False, 2)
         overlap = (512 * 512 / K) / (2 * np.pi * 25.0)
         pr = synth.Params(pk.mu, pk.chol, (pk.ea * min(1.0, overlap)).astype(np.float32), None)
-        for lr in (synth.PAPER_LR, fast):
-            rows.append(one(f"sparsity K={K}, SMoE", c2.target, pk, 10000, lr))
-            rows.append(one(f"sparsity K={K}, RBF", c2.target, pr, 10000, lr, rbf=True))
-    rows.append(one("config 2, fast rates", c2.target, c2.params, 10000, fast))
+        rows.append(one(f"sparsity K={K}, SMoE", c2.target, pk, 10000, lr2))
+        rows.append(one(f"sparsity K={K}, RBF", c2.target, pr, 10000, lr2, rbf=True))
     print(json.dumps({"metric": "fit PSNR and iterations/s on the paper-shaped workloads",
                       "mode": "quality", "rows": rows, "data": "synthetic", "dtype": "f32"}),
           flush=True)
@@ -519,6 +525,165 @@ def run_serve(args):
     }), flush=True)
 
 
+def _ragged_one(W, H, i):
+    """One image of the batched leg and its initial kernels (runs in a
+    spawned host process)."""
+    from paper_2510_05814_gb300 import synth
+    t = synth.polygon_image(W, H, 3, 40, 400 + i, texture_amp=0.1)
+    return t, synth.init_params(t, (W * H) // 16, 5.0, True, 400 + i)
+
+
+def _workload_2048(seed):
+    from paper_2510_05814_gb300 import synth
+    return synth.rgb_2048(seed=seed)
+
+
+def host_inputs(seed, n_ragged):
+    """The seeded inputs of the default run, drawn on the host cores in a
+    spawned process pool before this process touches the GPU: the 2048^2
+    workload and, with n_ragged > 0, the batched leg's ragged images."""
+    import multiprocessing as mp
+    from paper_2510_05814_gb300 import synth
+    sizes = synth.ragged_sizes(n_ragged, 4) if n_ragged else []
+    ctx = mp.get_context("spawn")
+    procs = max(1, min(len(sizes) + 1, os.cpu_count() or 1))
+    with ctx.Pool(procs) as pool:
+        wl = pool.apply_async(_workload_2048, (seed,))
+        imgs = pool.starmap(_ragged_one, [(W, H, i) for i, (W, H) in enumerate(sizes)])
+        wl = wl.get()
+    return wl, sizes, imgs
+
+
+def psnr_of_mse(mse):
+    import numpy as np
+    mse = np.asarray(mse, np.float64)
+    return 10.0 * np.log10(1.0 / np.maximum(mse, 1e-300))
+
+
+def fit_to_psnr_leg(wl, params0, iters, target_db, chunk=25):
+    """A whole fit of the 2048^2 workload from its initial kernels, the way a
+    caller runs it (FitBatch.run with CUDA-graph replays of `chunk`
+    iterations and the spatial re-sort every 25): CUDA events after every
+    chunk give the fit's device time at each point of its loss history
+    (the MSE of every iteration, before its update).  Returns the wall time,
+    the time to the first iteration whose MSE reaches `target_db` PSNR, and
+    the PSNR of the final model rendered and clamped to [0, 1]."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import api, synth
+    from paper_2510_05814_gb300.fit import FitBatch
+    C, H, W = wl.target.shape
+    tgt = torch.tensor(wl.target, device="cuda")
+    cap = None
+    for _attempt in range(4):
+        fb = FitBatch([tgt], [params0.clone()], iters, lr=synth.fit_rates(W, H), tile=wl.tile,
+                      qmax=wl.qmax, hist=iters, reorder_every=REORDER_EVERY, pair_cap=cap)
+        fb.capture(chunk)
+        n_chunks = iters // chunk
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_chunks + 1)]
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        ev[0].record()
+        for c in range(n_chunks):
+            fb.graph.replay()
+            fb.reorder()
+            ev[c + 1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - h0
+        if fb.status_code() == 0:
+            break
+        cap = 2 * fb.pair_cap                     # the lists outgrew the buffer: rerun larger
+    assert fb.status_code() == 0
+    t_at = np.array([ev[0].elapsed_time(e) / 1e3 for e in ev[1:]])
+    ps = psnr_of_mse(fb.losses()[0][: n_chunks * chunk])
+    hit = np.nonzero(ps >= target_db)[0]
+    t_hit = float(t_at[hit[0] // chunk]) if len(hit) else None
+    y, inv, _ = api.render(fb.params_of(0), W, H, tile=wl.tile, qmax=wl.qmax)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    api.smoe_sq_error(y, tgt, out, clamp=True)
+    final = float(psnr_of_mse(out.item() / y.numel()))
+    marks = [0, 100, 300, 1000, 2000, 5000, n_chunks * chunk - 1]
+    return {"iters": n_chunks * chunk, "lr": list(synth.fit_rates(W, H)),
+            "device_s": float(t_at[-1]), "wall_s": wall,
+            "iters_per_s": n_chunks * chunk / float(t_at[-1]),
+            "target_psnr_db": target_db, "s_to_target": t_hit,
+            "iters_to_target": int(hit[0]) + 1 if len(hit) else None,
+            "psnr_final_db": final, "psnr_max_db": float(ps.max()),
+            "uncovered_px": float((inv == 0).float().mean()),
+            "psnr_db_at": {int(i): round(float(ps[i]), 3) for i in marks if i < len(ps)},
+            "how": f"fresh fit from the initial kernels, graph replays of {chunk} iterations, "
+                   f"re-sort every {REORDER_EVERY}; PSNR per iteration from the fit's own MSE "
+                   "(before that iteration's update); final PSNR on the render clamped to [0,1]"}
+
+
+def batched_leg(sizes, imgs, iters, chunk=25):
+    """The ragged batch of 64 images (128x96 .. 1920x1080, K = pixels/16)
+    fitted as one batch (one launch per phase per iteration over the ragged
+    tile table, graph replays) against the same fits run one image per
+    launch, one after another.  Deterministic accumulation, so every image's
+    fit is the same bit for bit in both arms (equal PSNR).  All requests are
+    present at t = 0: a batched image's latency is the batch's time; a plain
+    image's latency is the time until its own fit ends."""
+    import numpy as np
+    import torch
+    from paper_2510_05814_gb300 import api, synth
+    from paper_2510_05814_gb300.fit import FitBatch
+    T = 16
+    targets = [torch.tensor(t, device="cuda") for t, _ in imgs]
+    params = [api.SMoEParams.from_numpy(p) for _, p in imgs]
+    lrs = [synth.fit_rates(W, H) for W, H in sizes]
+    pairs = 0
+    for (W, H), p in zip(sizes, params):
+        r = api.Rasterizer(api.RasterDesc(W, H, 3, T, True), p.K).bin(p)
+        pairs += evaluated_pairs(r.tile_off.cpu().numpy(), W, H, T)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fb = FitBatch(targets, [p.clone() for p in params], iters, lr=lrs, tile=T,
+                  deterministic=True, hist=iters)
+    fb.capture(chunk)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(iters // chunk):
+        fb.graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    assert fb.status_code() == 0
+    t_b = e0.elapsed_time(e1) / 1e3
+    mse_b = fb.losses()[:, iters - 1]
+    del fb
+    t_p, lat_p, mse_p = 0.0, [], []
+    for b in range(len(targets)):
+        one = FitBatch([targets[b]], [params[b].clone()], iters, lr=lrs[b], tile=T,
+                       deterministic=True, hist=iters)
+        one.capture(chunk)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(iters // chunk):
+            one.graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        assert one.status_code() == 0
+        t_p += e0.elapsed_time(e1) / 1e3
+        lat_p.append(t_p)
+        mse_p.append(one.losses()[0][iters - 1])
+        del one
+    dpsnr = float(np.max(np.abs(psnr_of_mse(mse_b) - psnr_of_mse(np.array(mse_p)))))
+    pct = lambda xs, q: float(np.percentile(xs, q))
+    return {"images": len(targets), "iters": iters, "tile": T, "launch": "grid, deterministic",
+            "pixels": int(sum(W * H for W, H in sizes)), "kernels": int(sum(p.K for p in params)),
+            "pairs_per_iter": int(pairs),
+            "batched": {"s": t_b, "value": pairs * iters / t_b / 1e9,
+                        "latency_p50_s": t_b, "latency_p99_s": t_b},
+            "plain": {"s": t_p, "value": pairs * iters / t_p / 1e9,
+                      "latency_p50_s": pct(lat_p, 50), "latency_p99_s": pct(lat_p, 99)},
+            "throughput_ratio": t_p / t_b,
+            "p99_latency_ratio": pct(lat_p, 99) / t_b,
+            "max_abs_psnr_diff_db": dpsnr,
+            "psnr_mean_db": float(np.mean(psnr_of_mse(mse_b))),
+            "unit": UNIT,
+            "how": f"{iters} iterations as graph replays of {chunk}; requests all at t = 0; "
+                   "plain images run one after another in the given order"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -530,6 +695,12 @@ def main():
                     help="reference arm crop side (0: sized so the run takes about 90 s)")
     ap.add_argument("--binned-crop", type=int, default=1024)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--fit-iters", type=int, default=10000,
+                    help="iterations of the fit-to-PSNR leg (0: skip)")
+    ap.add_argument("--fit-target-db", type=float, default=FIT_TARGET_DB)
+    ap.add_argument("--batched-images", type=int, default=64,
+                    help="images of the batched-vs-plain leg (0: skip)")
+    ap.add_argument("--batched-iters", type=int, default=25)
     ap.add_argument("--mode", default="fit",
                     choices=["fit", "batched", "serve", "denoise", "quality"],
                     help="fit: the 2048^2 fit step (default); batched: 64 ragged images; "
@@ -562,8 +733,21 @@ def main():
     if args.mode == "denoise":
         args.iters = args.iters or 2000
         return run_denoise(args)
+    return run_fit(args)
 
+
+def run_fit(args):
     import numpy as np
+    # host inputs first: the pool is spawned before this process uses the GPU
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    n_ragged = args.batched_images if (world == 1 and args.batched_images) else 0
+    if world == 1:
+        wl, rsizes, rimgs = host_inputs(replica_seed(rank), n_ragged)
+    else:
+        from paper_2510_05814_gb300 import synth
+        wl, rsizes, rimgs = synth.rgb_2048(seed=replica_seed(rank)), [], []
+
     import torch
     world, rank, local = dist_init()
     torch.cuda.set_device(local)
@@ -575,14 +759,15 @@ def main():
     from paper_2510_05814_gb300 import api
     from paper_2510_05814_gb300.fit import FitBatch
 
-    wl = synth.rgb_2048(seed=replica_seed(rank))
     C, H, W = wl.target.shape
     T = wl.tile
     tgt = torch.tensor(wl.target, device="cuda")
-    params = api.SMoEParams.from_numpy(wl.params)
+    params0 = api.SMoEParams.from_numpy(wl.params)
+    params = params0.clone()
+    lr = synth.fit_rates(W, H)
     n_phase = min(args.steps, 200)               # eager steps timed phase by phase
     total_iters = args.warmup + 2 * args.steps + n_phase + 5
-    fb = FitBatch([tgt], [params], total_iters, lr=synth.PAPER_LR, tile=T, qmax=wl.qmax,
+    fb = FitBatch([tgt], [params], total_iters, lr=lr, tile=T, qmax=wl.qmax,
                   hist=total_iters, reorder_every=REORDER_EVERY)
     desc = api.RasterDesc(W, H, C, T, True, wl.qmax, 1.0)
 
@@ -596,8 +781,7 @@ def main():
     torch.cuda.synchronize()
     assert fb.status_code() == 0
     pairs0, lists0, inrange0 = pairs_now()
-    rates = issue_rates()
-
+    rates0 = issue_rates()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     # The step as FitBatch.run(graph_iters=...) runs it: one CUDA-graph replay
@@ -618,6 +802,7 @@ def main():
                 fb.reorder()
             ev[s][1].record(stream)
         torch.cuda.synchronize()
+    rates1 = issue_rates()
     if world > 1:
         torch.distributed.barrier()
     # the same step launched phase by phase (eager), for the breakdown
@@ -653,73 +838,58 @@ def main():
     inrange_step = 0.5 * (inrange0 + inrange1)
     tot_s = sum(step_ms) / 1e3
 
-    # end to end through the public API with host buffers: per step the
-    # target goes host->device from pinned memory and the loss comes back.
-    # The copies run on their own stream into a double buffer, so step s+1's
-    # target moves while step s computes; every copy is inside the timed
-    # region (the first one starts after e0, the last loss lands before e1).
+    # End to end through the public API, as a caller resumes a fit: inside
+    # the timed region the target goes host -> device once (pinned memory),
+    # the steps run as graph replays (with the periodic re-sort), and the
+    # fitted parameters come back to pinned host memory in the caller's
+    # kernel order (params_of into preallocated buffers).
     host_t = torch.empty_like(tgt, device="cpu").pin_memory()
     host_t.copy_(tgt.cpu())
-    host_loss = torch.zeros(1, dtype=torch.float64).pin_memory()
-    bufs = [fb.targets[0], torch.empty_like(tgt)]
-    cstream = torch.cuda.Stream()
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
-    freed = [torch.cuda.Event(), torch.cuda.Event()]
-    # one captured iteration per target buffer (the target pointer is part of
-    # the captured launches), captured before the timed region
-    step_graph = []
-    for buf in bufs:
-        fb.set_target(0, buf)
-        step_graph.append(fb.capture(1))
+    gathered = params.zeros_like()
+    host_p = [torch.empty_like(t, device="cpu").pin_memory() for t in gathered.tensors()]
+    step_graph = fb.capture(1)
+    fb.params_of(0, out=gathered)               # warm the gather path outside the region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    cstream.wait_event(e0)
-    with torch.cuda.stream(cstream):
-        bufs[0].copy_(host_t, non_blocking=True)
-        ready[0].record(cstream)
+    fb.targets[0].copy_(host_t, non_blocking=True)
     for s in range(args.steps):
-        cur, nxt = s % 2, 1 - s % 2
-        if s + 1 < args.steps:
-            if s >= 1:
-                cstream.wait_event(freed[nxt])        # step s-1 is done with that buffer
-            with torch.cuda.stream(cstream):
-                bufs[nxt].copy_(host_t, non_blocking=True)
-                ready[nxt].record(cstream)
-        stream.wait_event(ready[cur])
-        it = int(args.warmup + 1 + args.steps + n_phase + s)
-        step_graph[cur].replay()
+        step_graph.replay()
         if (s + 1) % REORDER_EVERY == 0:
             fb.reorder()
-        freed[cur].record(stream)
-        host_loss.copy_(fb.loss[0, it:it + 1], non_blocking=True)
+    fb.params_of(0, out=gathered)
+    for h, d in zip(host_p, gathered.tensors()):
+        h.copy_(d, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) / 1e3
-    fb.set_target(0, bufs[0])
     assert fb.status_code() == 0
+    h2d = int(tgt.numel() * 4)
+    d2h = int(sum(t.numel() for t in gathered.tensors()) * 4)
+    del fb, graph, step_graph
 
-    # super-resolution render of the current model at 2x (4096 x 4096)
+    # super-resolution render of the initial model at 2x (4096 x 4096)
     sr_desc = api.RasterDesc(2 * W, 2 * H, C, T, True, wl.qmax, 2.0)
-    sr = api.Rasterizer(sr_desc, params.K, pair_cap=4 * fb.pair_cap).bin(fb.params_of(0))
+    sr = api.Rasterizer(sr_desc, params.K, pair_cap=8 * lists1).bin(params)
     y_sr, inv_sr = sr.render()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     f0.record(stream)
-    sr.bin(fb.params_of(0), check_capacity=False)
+    sr.bin(params, check_capacity=False)
     sr.render(y_sr, inv_sr)
     f1.record(stream)
     torch.cuda.synchronize()
     sr_ms = f0.elapsed_time(f1)
     sr_pairs = evaluated_pairs(sr.tile_off.cpu().numpy(), 2 * W, 2 * H, T)
+    del sr, y_sr, inv_sr
 
     # irregular-raster resampling at 10x magnification: a 205 x 205 crop of
-    # the current model on a jittered 10x raster (4.2 M points)
+    # the model on a jittered 10x raster (4.2 M points)
     g10 = (np.arange(2050) + 0.5) / 10.0
     pts = np.stack(np.meshgrid(900.0 + g10, 900.0 + g10), -1).reshape(-1, 2)
     pts += np.random.default_rng(11).uniform(-0.04, 0.04, pts.shape)
     pts = torch.tensor(pts, dtype=torch.float32, device="cuda")
-    rp = api.Rasterizer(desc, params.K, pair_cap=fb.pair_cap).bin(fb.params_of(0))
+    rp = api.Rasterizer(desc, params.K, pair_cap=2 * lists1).bin(params)
     yp, ip = rp.render_points(pts)
     torch.cuda.synchronize()
     f0.record(stream)
@@ -727,37 +897,40 @@ def main():
     f1.record(stream)
     torch.cuda.synchronize()
     pts_ms = f0.elapsed_time(f1)
+    del rp, yp, ip
 
     # job-wide aggregation (max time over ranks, summed work)
     tot_s, work, e2e_s = aggregate(tot_s, pairs_step * args.steps, e2e_s, world)
     value = work / tot_s / 1e9
     e2e_value = work / e2e_s / 1e9
 
+    fit_leg = batched = None
+    if rank == 0 and world == 1 and args.fit_iters:
+        fit_leg = fit_to_psnr_leg(wl, params0, args.fit_iters, args.fit_target_db)
+    if rank == 0 and world == 1 and rsizes:
+        batched = batched_leg(rsizes, rimgs, args.batched_iters)
+
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    sm_max = clocks.get("sm_max_mhz")
-    if not sm_max and os.path.exists(peaks_path):
-        sm_max = json.load(open(peaks_path)).get("sm_max_mhz")
-    sm_max = sm_max or 2070.0
-    sm_load = clocks.get("sm_mhz") or sm_max                      # median SM clock under load
-    mufu = rates["ex2"] if rates else MUFU_PER_CLK_PER_SM
-    ex2_peak = mufu * sms * sm_load * 1e6                          # ex2 / s
+    rl = [r for r in (rates0, rates1) if r]
+    # the SM clock measured live by the issue-rate kernels just before and
+    # just after the timed region (the 200 ms nvidia-smi poll sees too few
+    # samples of a short region)
+    clk_mhz = statistics.mean(r["clock_mhz"] for r in rl) if rl else (clocks.get("sm_mhz") or 2070.0)
+    mufu = statistics.mean(r["ex2"] for r in rl) if rl else MUFU_PER_CLK_PER_SM
+    ffma = statistics.mean(r["ffma"] for r in rl) if rl else 128.0
+    ex2_peak = mufu * sms * clk_mhz * 1e6                          # ex2 / s
+    fma_peak = ffma * sms * clk_mhz * 1e6                          # FP32 lane-ops / s
     tile_s = statistics.mean(tile_ms) / 1e3
-    ex2_achieved = 2.0 * pairs_step / tile_s                       # fwd + bwd: 2 ex2 / pair
-    # FP32 roofline on the pairs that contribute (q <= q_max): the algorithmic
-    # FP32 lane operations of one fwd+bwd pair, RGB linear, against the
-    # measured FFMA lane rate (listed pairs would exceed 1: culled pairs cost
-    # the kernel next to nothing)
-    ffma = rates["ffma"] if rates else 128.0
-    fma_peak = ffma * sms * sm_load * 1e6
-    fma_achieved = FP32_OPS_PER_PAIR * inrange_step / tile_s
+    fma_alg = FP32_OPS_PER_PAIR * inrange_step                     # per launch
     ncu = None
     if NCU["render_cu_code_sha256"] and NCU["render_cu_code_sha256"] == code_sha256(
             os.path.join(ROOT, "paper_2510_05814_gb300", "csrc", "render.cu")):
         ncu = NCU
     traffic = ncu["bytes_per_launch"] if ncu else None
+    basis = (f"{sms} SMs x {clk_mhz:.0f} MHz (SM clock measured live by libsmoe_rates before "
+             "and after the timed region)")
 
     cpu = cpu_binned = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -779,6 +952,7 @@ def main():
             "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "image": f"{W}x{H}x{C}", "K": params.K, "tile": T,
+                       "lr": list(lr),
                        "l2": "flushed (256 MiB write, untimed) before every timed step",
                        "launch": "one CUDA-graph replay of the whole fit iteration per step "
                                  "(the FitBatch.run(graph_iters=...) path)",
@@ -786,27 +960,38 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "pairs_per_step": int(pairs_step), "list_pairs": int(lists1),
                        "in_range_pairs_per_step": int(inrange_step)},
+            # the binding resource of the fused tile kernel: the FP32 pipe, on
+            # the method's work (pairs inside the cutoff)
             "roofline": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
-                         "achieved": ex2_achieved / 1e9, "peak": ex2_peak / 1e9,
-                         "unit": "Gex2/s", "frac": ex2_achieved / ex2_peak,
+                         "achieved": fma_alg / tile_s / 1e12, "peak": fma_peak / 1e12,
+                         "unit": "T FP32 lane-ops/s", "frac": fma_alg / tile_s / fma_peak,
                          "traffic": traffic,
-                         "peak_basis": (f"{mufu:.1f} ex2 lanes/clk/SM "
-                                        f"({'measured live, libsmoe_rates' if rates else 'fallback'})"
-                                        f" x {sms} SMs x {sm_load:.0f} MHz (median under load); "
-                                        "2 ex2 per listed fwd+bwd pair"),
-                         "issue_rates_per_clk_per_sm": rates,
-                         "ncu_pipes": None if ncu is None else {
-                             "fma_pipe_active": ncu["fma_pipe_active"],
-                             "issue_active": ncu["issue_active"],
-                             "xu_active": ncu["xu_active"]}},
-            "roofline_fma": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
-                             "achieved": fma_achieved / 1e12, "peak": fma_peak / 1e12,
-                             "unit": "T FP32 lane-ops/s", "frac": fma_achieved / fma_peak,
-                             "basis": (f"{FP32_OPS_PER_PAIR} FP32 lane operations per in-range "
-                                       "fwd+bwd pair (19 forward + 48 backward, RGB linear) x "
-                                       "in-range pairs / fused-kernel time; peak "
-                                       f"{ffma:.1f} FFMA lanes/clk/SM x {sms} SMs x "
-                                       f"{sm_load:.0f} MHz")},
+                         "per_unit": {"unit": "in-range (q <= q_max) fwd+bwd pixel-kernel pair",
+                                      "fp32_lane_ops": FP32_OPS_PER_PAIR,
+                                      "units_per_launch": int(inrange_step),
+                                      "launch_ms": tile_s * 1e3},
+                         "peak_basis": f"{ffma:.1f} FFMA lanes/clk/SM (libsmoe_rates, live) x "
+                                       + basis,
+                         "issue_rates_per_clk_per_sm": rl},
+            "roofline_ex2": {
+                "in_range": {"achieved": 2.0 * inrange_step / tile_s / 1e9,
+                             "peak": ex2_peak / 1e9, "unit": "Gex2/s",
+                             "frac": 2.0 * inrange_step / tile_s / ex2_peak,
+                             "basis": "2 ex2 per in-range fwd+bwd pair"},
+                "listed": {"achieved": 2.0 * pairs_step / tile_s / 1e9,
+                           "peak": ex2_peak / 1e9, "unit": "Gex2/s",
+                           "frac": 2.0 * pairs_step / tile_s / ex2_peak,
+                           "basis": "2 ex2 per listed pair (sum over tiles of pixels x list "
+                                    "length): the metric's pair count"},
+                "peak_basis": f"{mufu:.1f} ex2 lanes/clk/SM (libsmoe_rates, live) x " + basis},
+            "fp32_executed": None if ncu is None or not ncu.get("fp32_lane_ops") else {
+                "lane_ops_per_launch": ncu["fp32_lane_ops"],
+                "per_in_range_pair": ncu["fp32_lane_ops"] / inrange_step,
+                "achieved": ncu["fp32_lane_ops"] / tile_s / 1e12, "unit": "T FP32 lane-ops/s",
+                "frac": ncu["fp32_lane_ops"] / tile_s / fma_peak,
+                "source": "ncu sass thread-instruction counts of one launch (FFMA + FADD + "
+                          "FMUL + 2 x (FFMA2 + FADD2 + FMUL2)), profiles/",
+                "pipes": {k: ncu[k] for k in ("fma_pipe_active", "issue_active", "xu_active")}},
             "value_fwd_bwd_only": pairs_step / tile_s / 1e9,
             # pairs with q <= q_max (the ones that contribute) per second of the
             # fused tile kernel, and their share of the listed pairs
@@ -819,19 +1004,25 @@ def main():
                           "how": "the same step launched phase by phase (no graph), "
                                  "CUDA events between the phases"},
             "fit_iters_per_s": args.steps / tot_s,
+            "fit_to_psnr": fit_leg,
+            "batched_vs_plain": batched,
             "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
-                             "Gpairs_per_s": sr_pairs / sr_ms / 1e6},
+                             "Gpairs_per_s": sr_pairs / sr_ms / 1e6,
+                             "model": "the initial kernels"},
             "resample_points_10x": {"points": int(pts.shape[0]), "ms": pts_ms,
                                     "Gpoints_per_s": pts.shape[0] / pts_ms / 1e6,
                                     "raster": "jittered 10x raster over a 205x205 crop"},
             "cpu_baseline": cpu,
             "cpu_baseline_binned": cpu_binned,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(tgt.numel() * 4),
-                    "d2h_bytes_per_step": 8,
-                    "copies": "pinned host target -> device each step on a copy stream "
-                              "(double buffer, overlapping the previous step); loss -> host",
-                    "launch": "one CUDA-graph replay per step, one graph per target buffer "
-                              "(FitBatch.capture after set_target)",
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps,
+                    "h2d_bytes": h2d, "d2h_bytes": d2h,
+                    "copies": "the target host -> device once (pinned), the fitted parameters "
+                              "(14 floats per kernel, caller's order) device -> host once, "
+                              "both inside the timed region",
+                    "launch": "one CUDA-graph replay per step (FitBatch.capture), the periodic "
+                              "re-sort, params_of for the caller's order",
                     "l2": "not flushed: steps back to back, as a caller runs them"},
             "gpu_launches": KERNELS_PER_STEP * args.steps
                             + REORDER_KERNELS * (args.steps // REORDER_EVERY),

@@ -243,6 +243,32 @@ SMOE_API smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_
                                     int64_t pair_cap, void *ws, size_t ws_bytes, int32_t phase,
                                     int32_t *status, void *stream);
 
+/* The gradients of one fit iteration (Sec. III-D: gradient descent through
+ * the rasteriser), read out instead of applied: bins the batch's current
+ * parameters (phase 0), runs the fused forward / MSE / backward launch over
+ * the ragged tile table (phase 1, with the batch's persistent and
+ * deterministic settings), and turns every kernel's sums into dL/dtheta of
+ * that image's MSE, sum((y - target)^2) / (C H W), by the same device code
+ * the Adam launch of phase 2 uses, writing them to `grad` instead of
+ * updating the parameters.  Parameters, Adam moments, step counters and the
+ * loss history are left as they are, and the workspace's gradient sums are
+ * zero again afterwards, so the fit can continue with smoe_fit.
+ *   batch, imgs, pair_cap, ws, ws_bytes: as smoe_fit_phase, after
+ *              smoe_fit_init on this workspace
+ *   grad       out: one parameter set of K_total = sum_b imgs[b].p.K rows
+ *              (device SoA), image b's kernels at rows sum_{b' < b} K_b' ..,
+ *              in the order of the batch's parameter arrays; mu in the
+ *              normalised units of smoe_params; eW set iff the experts are
+ *              linear; logpi optional (when set: dL/dlogpi, at pi = 1 for
+ *              images without gate weights).  Kernels of an image whose run
+ *              has ended (step >= iters) get 0.
+ *   status     device status word: a pair count above pair_cap sets
+ *              SMOE_ERR_CAPACITY and grad is then not written
+ * Returns SMOE_ERR_ARG for a grad whose K or groups do not match. */
+SMOE_API smoe_status smoe_fit_gradients(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                                        int64_t pair_cap, void *ws, size_t ws_bytes,
+                                        const smoe_params *grad, int32_t *status, void *stream);
+
 /* Multi-model fusion for denoising (Sec. V-C, Eq. 11): y_m = (1/H) sum_h y_h,
  * the per-pixel mean of the renders of the H = batch->B models of a fit
  * batch whose images all have one size W x H (the H models of MM-RSMoE are
@@ -323,16 +349,18 @@ SMOE_API smoe_status smoe_render_mean(const smoe_desc *d, const smoe_params *mod
 /* Native sharpening by kernel editing (Sec. II-B, Sec. VII-C): the kernel
  * bandwidths divided by a sharpening factor f, i.e. L' = f L (P' = f^2 P):
  * chol_out[i] = f * chol_in[i] for the 3K entries, each rounded to float
- * once.  Render the edited model with q_max' = q_max * f * f (float
- * products) so each kernel keeps the support of the fitted model and only
- * the gates steepen (f > 1 sharpens edges; flat regions keep their value).
- * q_max' must stay <= 174 (f <= 4.39 for q_max = 9): beyond it the gate of a
- * far included pair leaves the FP32 range.
+ * once, and the cutoff to render the edited model with,
+ * *qmax_out = qmax * (f * f) (two FP32 products), so that each kernel keeps
+ * the support of the fitted model and only the gates steepen (f > 1 sharpens
+ * edges; flat regions keep their value).
  *   chol_in, chol_out: K x 3 FP32 (device); they may be the same buffer
- *   factor: finite, > 0
- * Returns SMOE_ERR_ARG for a bad K or factor. */
+ *   factor: finite, > 0;  qmax: the fitted model's cutoff, > 0
+ *   qmax_out: out, one float (host)
+ * Returns SMOE_ERR_ARG for a bad K, factor or qmax, or when q_max' exceeds
+ * 174 (f <= 4.39 for q_max = 9), where the gate of a far included pair would
+ * leave the FP32 range; nothing is written then. */
 SMOE_API smoe_status smoe_sharpen(const float *chol_in, float *chol_out, int64_t K,
-                                  float factor, void *stream);
+                                  float factor, float qmax, float *qmax_out, void *stream);
 
 /* Bytes of the scratch that smoe_render_points needs for n_points points on
  * the raster of d. */
@@ -376,6 +404,7 @@ SMOE_API smoe_status smoe_count_inrange(const smoe_desc *d, int64_t K, const voi
  * no counterpart; it is smoe_bin followed by smoe_render with every
  * intermediate buffer in one fixed 8 MiB device array inside the library,
  * which every GPU that loads the library holds until the process exits.
+ *   The raster checks are smoe_render's (SMOE_ERR_ARG, q_max <= 174 included).
  *   Limits: K <= 32768 kernels, at most 16384 tiles on the output raster
  *   (e.g. 2048x2048 at tile 16), at most 524288 (tile, kernel) pairs.
  *   Larger K or rasters are refused with SMOE_ERR_WORKSPACE before any work;
@@ -383,9 +412,11 @@ SMOE_API smoe_status smoe_count_inrange(const smoe_desc *d, int64_t K, const voi
  *   device and y / inv_d are then not written.
  *   p      parameters (device SoA); y: C x H x W out; inv_d: H x W out or NULL
  *   status out: one int32 (device), zeroed by the call, then as smoe_bin.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps the
+ * Outside stream capture every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, so a device reset leaves no
+ * stale address; a call under capture uses the address of the last call on
+ * that device outside capture, so make the first call on a device before any
+ * stream capture.  All calls share the one array and it keeps the
  * last call's contents, so calls whose work overlaps on the GPU (different
  * streams, or different host threads on one device) race: serialise them.
  * The call itself allocates nothing and does not synchronise. */

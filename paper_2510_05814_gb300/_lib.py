@@ -14,6 +14,7 @@ STATUS_NAMES = {0: "SMOE_OK", 1: "SMOE_ERR_ARG", 2: "SMOE_ERR_CAPACITY", 3: "SMO
 EXPORTS = ["smoe_version", "smoe_workspace_size", "smoe_bin", "smoe_render",
            "smoe_render_backward", "smoe_adam_step", "smoe_sq_error",
            "smoe_fit_workspace_size", "smoe_fit_init", "smoe_fit", "smoe_fit_phase",
+           "smoe_fit_gradients",
            "smoe_fit_render_mean", "smoe_render_mean_workspace_size", "smoe_render_mean",
            "smoe_sharpen", "smoe_points_workspace_size",
            "smoe_render_points", "smoe_count_inrange", "smoe_render_static",
@@ -83,10 +84,12 @@ def load():
         "smoe_fit_init": (I32, [FB, FI, I64, P, ctypes.c_size_t, I32, P, P]),
         "smoe_fit": (I32, [FB, FI, I64, P, ctypes.c_size_t, I32, P, P]),
         "smoe_fit_phase": (I32, [FB, FI, I64, P, ctypes.c_size_t, I32, P, P]),
+        "smoe_fit_gradients": (I32, [FB, FI, I64, P, ctypes.c_size_t, PP, P, P]),
         "smoe_fit_render_mean": (I32, [FB, FI, I64, P, ctypes.c_size_t, P, P, P]),
         "smoe_render_mean_workspace_size": (I32, [D, PP, I32, I64, SZ]),
         "smoe_render_mean": (I32, [D, PP, I32, P, ctypes.c_size_t, I64, P, P, P]),
-        "smoe_sharpen": (I32, [P, P, I64, ctypes.c_float, P]),
+        "smoe_sharpen": (I32, [P, P, I64, ctypes.c_float, ctypes.c_float,
+                                ctypes.POINTER(ctypes.c_float), P]),
         "smoe_points_workspace_size": (I32, [D, I64, ctypes.POINTER(ctypes.c_size_t)]),
         "smoe_render_points": (I32, [D, I64, P, ctypes.c_size_t, P, P, I64, P, P,
                                      ctypes.c_size_t, P, P, P, P]),

@@ -264,20 +264,21 @@ class Rasterizer:
 
 
 def sharpen(params: SMoEParams, factor: float, qmax: float = 9.0):
-    """Native sharpening by kernel editing (Sec. II-B): a model whose kernel
-    bandwidths are divided by ``factor`` (L' = factor L, on the GPU; mu and
-    the experts are shared with ``params``) and the cutoff that keeps each
-    kernel's support, q_max' = q_max factor^2 (float32 products).  Returns
-    (sharpened params, q_max')."""
-    f32 = np.float32(factor)
-    qmax2 = float(np.float32(qmax) * (f32 * f32))
-    if not qmax2 <= 174.0:
-        raise ValueError(f"sharpening {factor} x at q_max {qmax} needs q_max' = {qmax2} > 174, "
-                         "beyond the FP32 range of the gates")
+    """Native sharpening by kernel editing (Sec. II-B, smoe_sharpen): a model
+    whose kernel bandwidths are divided by ``factor`` (L' = factor L, on the
+    GPU; mu and the experts are shared with ``params``) and the cutoff that
+    keeps each kernel's support, q_max' = q_max factor^2, both from the
+    library.  Returns (sharpened params, q_max').  Raises ValueError where
+    the library refuses the factor (q_max' beyond the FP32 range of the
+    gates)."""
     chol = torch.empty_like(params.chol)
-    check(_lib.load().smoe_sharpen(_ptr(params.chol), _ptr(chol), params.K, float(factor),
-                                   _stream(None)), "smoe_sharpen")
-    return SMoEParams(params.mu, chol, params.ea, params.eW), qmax2
+    q2 = ctypes.c_float(0.0)
+    code = _lib.load().smoe_sharpen(_ptr(params.chol), _ptr(chol), params.K, float(factor),
+                                    float(qmax), ctypes.byref(q2), _stream(None))
+    if code == _lib.SMOE_ERR_ARG:
+        raise ValueError(f"smoe_sharpen refused factor {factor} at q_max {qmax}")
+    check(code, "smoe_sharpen")
+    return SMoEParams(params.mu, chol, params.ea, params.eW), float(q2.value)
 
 
 def render(params: SMoEParams, W, H, tile=16, qmax=9.0, scale=1.0, sharpen_factor=None,

@@ -28,7 +28,10 @@ class TuneResult:
 
 def groups_by_kernels(Ks, max_kernels):
     """Consecutive groups of images with at most max_kernels kernels each
-    (an image larger than the limit gets a group of its own)."""
+    (an image larger than the limit gets a group of its own); no images, no
+    groups."""
+    if not Ks:
+        return []
     if not max_kernels:
         return [list(range(len(Ks)))]
     out, cur, n = [], [], 0

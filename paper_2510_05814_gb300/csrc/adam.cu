@@ -196,14 +196,79 @@ __device__ __forceinline__ void adam_uniform(const ImgDev &im, const Betas &be, 
     }
 }
 
+// The gradient of kernel k (global id, image im) in API units, from its raw
+// per-kernel sums (the float-atomic sums, or in deterministic mode the
+// per-pair partials added in tile order) and its prepared record: the chain
+// rule of Eqs. 2-4 (the sums and their formulas are listed in render.cu),
+// the centre's gradient in normalised units (x W, x H).  Zeroes the kernel's
+// atomic sums for the next iteration.  A kernel listed in no tile touched no
+// pixel, so its gradient is exactly 0 (and must not become inf * 0 for
+// non-finite parameters).  Adam (k_fit_adam) and the gradient read-out
+// (k_fit_grads) both take their gradients from here.
 template <int C, bool LIN>
-__global__ void __launch_bounds__(kAdamThreads, 2)
-k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2, Betas be, int32_t *step,
-           uint32_t *done, float *coef) {
+struct KGrad {
+    static constexpr int NW = LIN ? 2 * C : 0;
+    float mu[2], chol[3], ea[C], eW[NW > 0 ? NW : 1], pi;
+};
+
+template <int C, bool LIN>
+__device__ __forceinline__ void kernel_grad(const Bufs &w, const ImgDev &im, int64_t k,
+                                            KGrad<C, LIN> &o) {
     constexpr int E = LIN ? 3 : 1;
     constexpr int S = (7 + C * E + 3) & ~3;       // record stride (floats)
     constexpr int GS = (6 + C * E + 3) & ~3;      // sums stride (floats)
     constexpr int PI = 5 + C * E;                 // dL/dlogpi slot
+    const int4 rc = w.rect[k];
+    const bool listed = rc.x <= rc.z;
+    float s[GS];
+    float4 *acc = reinterpret_cast<float4 *>(w.acc + k * GS);
+    if (!listed) {
+#pragma unroll
+        for (int q = 0; q < GS; ++q) s[q] = 0.0f;
+    } else if (w.part) {
+        gather_sums<GS>(w, im, k, rc, s);
+    } else {
+#pragma unroll
+        for (int q = 0; q < GS / 4; ++q) {
+            const float4 v = acc[q];
+            s[4 * q] = v.x; s[4 * q + 1] = v.y; s[4 * q + 2] = v.z; s[4 * q + 3] = v.w;
+        }
+    }
+    float r[S];
+    const float4 *rec = reinterpret_cast<const float4 *>(w.rec + k * S);
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) {
+        const float4 v = rec[q];
+        r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    }
+    float gmx = 0.f, gmy = 0.f;
+    if (listed) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+        o.ea[ch] = s[5 + ch];
+        if (LIN) {
+            if (listed) {
+                gmx -= r[7 + ch * E + 1] * s[5 + ch];
+                gmy -= r[7 + ch * E + 2] * s[5 + ch];
+            }
+#pragma unroll
+            for (int d = 0; d < 2; ++d) o.eW[2 * ch + d] = s[5 + (1 + d) * C + ch];
+        }
+    }
+    o.mu[0] = gmx * (float)im.W;
+    o.mu[1] = gmy * (float)im.H;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) o.chol[d] = -s[d];
+    o.pi = s[PI];                                 // dL/dlogpi = S0
+    if (!w.part && listed)     // an unlisted kernel's sums received nothing: still 0
+#pragma unroll
+        for (int q = 0; q < GS / 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+template <int C, bool LIN>
+__global__ void __launch_bounds__(kAdamThreads, 2)
+k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2, Betas be, int32_t *step,
+           uint32_t *done, float *coef) {
     constexpr int NW = LIN ? 2 * C : 0;           // slopes per kernel
     // gradient groups in shared memory: mu (2), chol (3), ea (C), eW (2C), logpi (1)
     constexpr int O_MU = 0, O_CH = O_MU + 2 * kAdamThreads, O_EA = O_CH + 3 * kAdamThreads;
@@ -223,54 +288,20 @@ k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2, Betas be
         }
         kimg[tid] = bk;
         if (bk >= 0) {
-            const ImgDev &im = img_of(g, bk);
-            // A kernel listed in no tile touched no pixel: its gradient is 0
-            // (and must not become inf * 0 for non-finite parameters).
-            const int4 rc = w.rect[k];
-            const bool listed = rc.x <= rc.z;
-            float s[GS];
-            float4 *acc = reinterpret_cast<float4 *>(w.acc + k * GS);
-            if (!listed) {
-#pragma unroll
-                for (int q = 0; q < GS; ++q) s[q] = 0.0f;
-            } else if (w.part) {
-                gather_sums<GS>(w, im, k, rc, s);
-            } else {
-#pragma unroll
-                for (int q = 0; q < GS / 4; ++q) {
-                    const float4 v = acc[q];
-                    s[4 * q] = v.x; s[4 * q + 1] = v.y; s[4 * q + 2] = v.z; s[4 * q + 3] = v.w;
-                }
-            }
-            float r[S];
-            const float4 *rec = reinterpret_cast<const float4 *>(w.rec + k * S);
-#pragma unroll
-            for (int q = 0; q < S / 4; ++q) {
-                const float4 v = rec[q];
-                r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
-            }
-            float gmx = 0.f, gmy = 0.f;
-            if (listed) { gmx = r[2] * s[3]; gmy = fmaf(r[3], s[3], r[4] * s[4]); }
+            KGrad<C, LIN> kg;
+            kernel_grad<C, LIN>(w, img_of(g, bk), k, kg);
 #pragma unroll
             for (int ch = 0; ch < C; ++ch) {
-                gsm[O_EA + tid * C + ch] = s[5 + ch];
-                if (LIN) {
-                    if (listed) {
-                        gmx -= r[7 + ch * E + 1] * s[5 + ch];
-                        gmy -= r[7 + ch * E + 2] * s[5 + ch];
-                    }
+                gsm[O_EA + tid * C + ch] = kg.ea[ch];
+                if (LIN)
 #pragma unroll
-                    for (int d = 0; d < 2; ++d) gsm[O_EW + tid * NW + 2 * ch + d] = s[5 + (1 + d) * C + ch];
-                }
+                    for (int d = 0; d < 2; ++d) gsm[O_EW + tid * NW + 2 * ch + d] = kg.eW[2 * ch + d];
             }
-            gsm[O_MU + 2 * tid] = gmx * (float)im.W;
-            gsm[O_MU + 2 * tid + 1] = gmy * (float)im.H;
+            gsm[O_MU + 2 * tid] = kg.mu[0];
+            gsm[O_MU + 2 * tid + 1] = kg.mu[1];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) gsm[O_CH + 3 * tid + d] = -s[d];
-            gsm[O_PI + tid] = s[PI];                       // dL/dlogpi = S0
-            if (!w.part && listed)     // an unlisted kernel's sums received nothing: still 0
-#pragma unroll
-                for (int q = 0; q < GS / 4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int d = 0; d < 3; ++d) gsm[O_CH + 3 * tid + d] = kg.chol[d];
+            gsm[O_PI + tid] = kg.pi;
         }
     }
     // One image for the whole CTA (and it is running): the single-round-trip update.
@@ -306,6 +337,33 @@ k_fit_adam(const __grid_constant__ Geo g, Bufs w, double b1, double b2, Betas be
         if (threadIdx.x == 0) *done = 0u;
         __threadfence();
     }
+}
+
+// Gradient read-out of the fit: the gradients that k_fit_adam would apply
+// this iteration (same sums, same kernel_grad), written to the caller's
+// arrays at the kernel's global (batch) index instead of stepping Adam.
+// Kernels of an image whose run has ended get 0 (its tiles were skipped).
+template <int C, bool LIN>
+__global__ void __launch_bounds__(kAdamThreads)
+k_fit_grads(const __grid_constant__ Geo g, Bufs w, const int32_t *step, smoe_params grad) {
+    constexpr int NW = LIN ? 2 * C : 0;
+    if (status_bad(w.status)) return;
+    const int64_t k = (int64_t)blockIdx.x * kAdamThreads + threadIdx.x;
+    if (k >= g.K_total) return;
+    const int b = img_by_kernel(g, k);
+    const ImgDev &im = img_of(g, b);
+    KGrad<C, LIN> kg{};
+    if (step[b] < im.iters) kernel_grad<C, LIN>(w, im, k, kg);
+    grad.mu[2 * k] = kg.mu[0];
+    grad.mu[2 * k + 1] = kg.mu[1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) grad.chol[3 * k + d] = kg.chol[d];
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) grad.ea[k * C + ch] = kg.ea[ch];
+    if (LIN)
+#pragma unroll
+        for (int i = 0; i < NW; ++i) grad.eW[k * NW + i] = kg.eW[i];
+    if (grad.logpi) grad.logpi[k] = kg.pi;
 }
 
 __global__ void k_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out) {
@@ -358,6 +416,17 @@ cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, d
     else if (g.C == 1) k_fit_adam<1, true><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
     else if (!g.linear) k_fit_adam<3, false><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
     else k_fit_adam<3, true><<<blocks, kAdamThreads, 0, st>>>(g, w, b1, b2, be, step, done, coef);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_grads(const Geo &g, const Bufs &w, const int32_t *step,
+                             const smoe_params &grad, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((g.K_total + kAdamThreads - 1) / kAdamThreads);
+    if (blocks == 0) return cudaSuccess;
+    if (g.C == 1 && !g.linear) k_fit_grads<1, false><<<blocks, kAdamThreads, 0, st>>>(g, w, step, grad);
+    else if (g.C == 1) k_fit_grads<1, true><<<blocks, kAdamThreads, 0, st>>>(g, w, step, grad);
+    else if (!g.linear) k_fit_grads<3, false><<<blocks, kAdamThreads, 0, st>>>(g, w, step, grad);
+    else k_fit_grads<3, true><<<blocks, kAdamThreads, 0, st>>>(g, w, step, grad);
     return cudaGetLastError();
 }
 

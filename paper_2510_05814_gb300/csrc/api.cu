@@ -11,10 +11,6 @@ using namespace smoe;
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int64_t kMaxTiles = 4096LL * 4096LL;   // prefix-sum capacity (4096 chunks)
-// Largest cutoff: exp(-q/2) of an included pair stays an FP32 normal number
-// (q log2(e) / 2 <= 125.5), so no included kernel is flushed to zero.
-constexpr float kMaxQmax = 174.0f;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -59,18 +55,7 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
     return L;
 }
 
-bool desc_ok(const smoe_desc *d) {
-    if (!d) return false;
-    if (d->W <= 0 || d->H <= 0) return false;
-    if (d->C != 1 && d->C != 3) return false;
-    if (d->tile != 8 && d->tile != 16 && d->tile != 32) return false;
-    if (d->expert != 0 && d->expert != 1) return false;
-    if (d->gate != 0 && d->gate != 1) return false;
-    if (!(d->qmax > 0.0f) || !(d->qmax <= kMaxQmax)) return false;
-    if (!(d->scale > 0.0f) || !std::isfinite(d->scale)) return false;
-    if (tiles_of(d->W, d->H, d->tile) > kMaxTiles) return false;
-    return true;
-}
+bool desc_ok(const smoe_desc *d) { return desc_valid(d); }
 
 bool params_ok(const smoe_params *p, const smoe_desc *d) {
     if (!p || p->K < 0 || p->K > 0x7fffffffLL) return false;
@@ -414,6 +399,27 @@ smoe_status smoe_fit_phase(const smoe_fit_batch *batch, const smoe_fit_image *im
         fit_phase(batch, g, w, done, coef, phase, static_cast<cudaStream_t>(stream)));
 }
 
+smoe_status smoe_fit_gradients(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
+                               int64_t pair_cap, void *ws, size_t ws_bytes,
+                               const smoe_params *grad, int32_t *status, void *stream) {
+    Geo g;
+    Bufs w;
+    Layout L;
+    std::vector<ImgDev> tab;
+    smoe_status s = fit_bufs(batch, imgs, pair_cap, ws, ws_bytes, status, &g, &w, &L, &tab);
+    if (s != SMOE_OK) return s;
+    if (!grad || grad->K != g.K_total) return SMOE_ERR_ARG;
+    if (g.K_total > 0 && (!grad->mu || !grad->chol || !grad->ea ||
+                          (grad->eW != nullptr) != (batch->expert == 1)))
+        return SMOE_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_bin(g, w, st);
+    if (e == cudaSuccess)
+        e = launch_fit_tiles(g, w, nullptr, 0, batch->step, batch->persistent != 0, st);
+    if (e == cudaSuccess) e = launch_fit_grads(g, w, batch->step, *grad, st);
+    return cuda_status(e);
+}
+
 smoe_status smoe_fit_render_mean(const smoe_fit_batch *batch, const smoe_fit_image *imgs,
                                  int64_t pair_cap, void *ws, size_t ws_bytes, float *y,
                                  int32_t *status, void *stream) {
@@ -456,10 +462,15 @@ smoe_status smoe_scatter_params(const smoe_params *src, const int32_t *index, in
 }
 
 smoe_status smoe_sharpen(const float *chol_in, float *chol_out, int64_t K, float factor,
-                         void *stream) {
+                         float qmax, float *qmax_out, void *stream) {
     if (K < 0 || K > 0x7fffffffLL || !(factor > 0.0f) || !std::isfinite(factor) ||
-        (K > 0 && (!chol_in || !chol_out)))
+        (K > 0 && (!chol_in || !chol_out)) || !qmax_out)
         return SMOE_ERR_ARG;
+    // q_max' = q_max f^2, two FP32 products (f^2 first), so that every point
+    // the fitted model includes stays included.
+    const float q2 = qmax * (factor * factor);
+    if (!(qmax > 0.0f) || !(q2 <= kMaxQmax)) return SMOE_ERR_ARG;
+    *qmax_out = q2;
     return cuda_status(launch_scale(chol_in, chol_out, 3 * K, factor,
                                     static_cast<cudaStream_t>(stream)));
 }

@@ -20,11 +20,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "../../include/smoe.h"
 
 namespace smoe {
 
 constexpr int kMaxC = 3;
+// Largest cutoff: exp(-q/2) of an included pair stays an FP32 normal number
+// (q log2(e) / 2 <= 125.5), so no included kernel is flushed to zero.
+constexpr float kMaxQmax = 174.0f;
+// Largest tile table of one launch (the prefix sum's capacity, 4096 chunks).
+constexpr int64_t kMaxTiles = 4096LL * 4096LL;
+
+// A raster description every entry point accepts (host side): positive
+// size, C 1 or 3, tile 8 / 16 / 32, known expert and gate modes, a cutoff in
+// (0, kMaxQmax], a finite positive scale and a tile count within kMaxTiles.
+inline bool desc_valid(const smoe_desc *d) {
+    if (!d) return false;
+    if (d->W <= 0 || d->H <= 0) return false;
+    if (d->C != 1 && d->C != 3) return false;
+    if (d->tile != 8 && d->tile != 16 && d->tile != 32) return false;
+    if (d->expert != 0 && d->expert != 1) return false;
+    if (d->gate != 0 && d->gate != 1) return false;
+    if (!(d->qmax > 0.0f) || !(d->qmax <= kMaxQmax)) return false;
+    if (!(d->scale > 0.0f) || !std::isfinite(d->scale)) return false;
+    const int64_t tiles = (int64_t)((d->W + d->tile - 1) / d->tile) * ((d->H + d->tile - 1) / d->tile);
+    return tiles <= kMaxTiles;
+}
 constexpr float kNegHalfLog2e = -0.72134752044448170368f;   // -log2(e) / 2
 constexpr float kLog2e = 1.44269504088896340736f;
 
@@ -204,6 +227,11 @@ cudaError_t launch_adam_soa(const smoe_params &p, const smoe_params &gr, const s
                             double eps, int32_t step, cudaStream_t st);
 cudaError_t launch_fit_adam(const Geo &g, const Bufs &w, double b1, double b2, double eps,
                             int32_t *step, uint32_t *done, float *coef, cudaStream_t st);
+// The finalized gradients of the fit's current iteration (the sums of the
+// fused tile launch through the same chain rule as launch_fit_adam) written
+// to grad at the batch's global kernel index; zeroes the atomic sums.
+cudaError_t launch_fit_grads(const Geo &g, const Bufs &w, const int32_t *step,
+                             const smoe_params &grad, cudaStream_t st);
 cudaError_t launch_adam_coefs(const Geo &g, const int32_t *step, double b1, double b2,
                               float *coef, cudaStream_t st);
 cudaError_t launch_sq_error(const float *y, const float *t, int64_t n, int clamp, double *out,

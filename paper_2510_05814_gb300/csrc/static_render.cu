@@ -7,7 +7,6 @@
 // sums and the (tile, kernel) lists) lives in one file-scope device array of
 // fixed size that every GPU loading this library holds until the process
 // exits.
-#include <cmath>
 #include <mutex>
 
 #include "smoe_internal.cuh"
@@ -17,43 +16,49 @@ namespace {
 using namespace smoe;
 
 // Limits of the static scratch.
-constexpr int64_t kMaxK = 32768;          // kernels
-constexpr int64_t kMaxTiles = 16384;      // tiles of the output raster
-constexpr int64_t kMaxPairs = 524288;     // (tile, kernel) pairs
+constexpr int64_t kStaticMaxK = 32768;          // kernels
+constexpr int64_t kStaticMaxTiles = 16384;      // tiles of the output raster
+constexpr int64_t kStaticMaxPairs = 524288;     // (tile, kernel) pairs
 constexpr size_t kScratchBytes = 8u << 20;
 
 constexpr size_t up(size_t x) { return (x + 255) & ~size_t(255); }
 // Region offsets inside the scratch (records sized for the widest record,
 // 16 floats: RGB with linear experts).
 constexpr size_t kRec = 0;
-constexpr size_t kRect = kRec + up(sizeof(float) * 16 * kMaxK);
-constexpr size_t kTileCnt = kRect + up(sizeof(int4) * kMaxK);
-constexpr size_t kCursor = kTileCnt + up(sizeof(int32_t) * kMaxTiles);
-constexpr size_t kLongQ = kCursor + up(sizeof(int32_t) * kMaxTiles);
-constexpr size_t kNLong = kLongQ + up(sizeof(int32_t) * kMaxTiles);
+constexpr size_t kRect = kRec + up(sizeof(float) * 16 * kStaticMaxK);
+constexpr size_t kTileCnt = kRect + up(sizeof(int4) * kStaticMaxK);
+constexpr size_t kCursor = kTileCnt + up(sizeof(int32_t) * kStaticMaxTiles);
+constexpr size_t kLongQ = kCursor + up(sizeof(int32_t) * kStaticMaxTiles);
+constexpr size_t kNLong = kLongQ + up(sizeof(int32_t) * kStaticMaxTiles);
 constexpr size_t kBsum = kNLong + up(sizeof(int32_t));
-constexpr size_t kTileOff = kBsum + up(sizeof(long long) * ((kMaxTiles + 4095) / 4096));
-constexpr size_t kNPairs = kTileOff + up(sizeof(int32_t) * (kMaxTiles + 1));
+constexpr size_t kTileOff = kBsum + up(sizeof(long long) * ((kStaticMaxTiles + 4095) / 4096));
+constexpr size_t kNPairs = kTileOff + up(sizeof(int32_t) * (kStaticMaxTiles + 1));
 constexpr size_t kPairTmp = kNPairs + up(sizeof(int64_t));
-constexpr size_t kPairK = kPairTmp + up(sizeof(int32_t) * kMaxPairs);
-constexpr size_t kEnd = kPairK + up(sizeof(int32_t) * kMaxPairs);
+constexpr size_t kPairK = kPairTmp + up(sizeof(int32_t) * kStaticMaxPairs);
+constexpr size_t kEnd = kPairK + up(sizeof(int32_t) * kStaticMaxPairs);
 static_assert(kEnd <= kScratchBytes, "static scratch layout exceeds its size");
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol: its device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch, looked up once per device.
+// Device address of g_scratch per device.  Outside stream capture it is
+// looked up again on every call (a cheap driver query), so a context that
+// was torn down and re-created (for example after cudaDeviceReset) cannot
+// leave a stale address behind; a call under capture uses the address of the
+// last call outside capture on that device.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
-smoe_status scratch_address(void **out) {
+smoe_status scratch_address(cudaStream_t st, void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return SMOE_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SMOE_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return SMOE_ERR_CUDA;
         g_addr[dev] = p;
@@ -67,12 +72,9 @@ smoe_status scratch_address(void **out) {
 extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smoe_params *p,
                                                    float *y, float *inv_d, int32_t *status,
                                                    void *stream) {
-    if (!d || !p || !y || !status) return SMOE_ERR_ARG;
-    if (d->W <= 0 || d->H <= 0 || (d->C != 1 && d->C != 3) ||
-        (d->tile != 8 && d->tile != 16 && d->tile != 32) || (d->expert != 0 && d->expert != 1) ||
-        (d->gate != 0 && d->gate != 1) ||
-        !(d->qmax > 0.0f) || !(d->scale > 0.0f) || !std::isfinite(d->scale))
-        return SMOE_ERR_ARG;
+    // The same raster checks as every other entry point (including the
+    // largest cutoff, beyond which an included pair's gate would flush to 0).
+    if (!desc_valid(d) || !p || !y || !status) return SMOE_ERR_ARG;
     if (p->K < 0 || (p->K > 0 && (!p->mu || !p->chol || !p->ea)) ||
         ((p->eW != nullptr) != (d->expert == 1) && p->K > 0))
         return SMOE_ERR_ARG;
@@ -80,13 +82,13 @@ extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smo
     const int tiles_y = (d->H + d->tile - 1) / d->tile;
     const int64_t tiles = (int64_t)tiles_x * tiles_y;
     // Beyond the static scratch: refuse (the caller needs smoe_bin + smoe_render).
-    if (p->K > kMaxK || tiles > kMaxTiles) return SMOE_ERR_WORKSPACE;
+    if (p->K > kStaticMaxK || tiles > kStaticMaxTiles) return SMOE_ERR_WORKSPACE;
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
     void *base = nullptr;
-    smoe_status s = scratch_address(&base);
+    smoe_status s = scratch_address(st, &base);
     if (s != SMOE_OK) return s;
     char *b = static_cast<char *>(base);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     Geo g{};
     g.C = d->C;
@@ -121,7 +123,7 @@ extern "C" SMOE_API smoe_status smoe_render_static(const smoe_desc *d, const smo
     w.pair_tmp = reinterpret_cast<int32_t *>(b + kPairTmp);
     w.pair_k = reinterpret_cast<int32_t *>(b + kPairK);
     w.acc = nullptr;
-    w.pair_cap = kMaxPairs;
+    w.pair_cap = kStaticMaxPairs;
     w.status = status;
 
     // The previous call's contents are stale: the status starts at 0, the

@@ -55,7 +55,7 @@ def init_models(noisy: np.ndarray, n_models: int, K: int, sigma: float = 5.0,
             for h, off in enumerate(shift_offsets(n_models, block))]
 
 
-def mm_rsmoe(noisy: torch.Tensor, models, iters: int, lr=synth.PAPER_LR, tile: int = 16,
+def mm_rsmoe(noisy: torch.Tensor, models, iters: int, lr=None, tile: int = 16,
              qmax: float = 9.0, graph_iters: int | None = None, deterministic: bool = False,
              persistent: bool = False):
     """Fit the H models (list of SMoEParams, updated in place) to the one

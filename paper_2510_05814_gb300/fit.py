@@ -21,7 +21,9 @@ class FitBatch:
     targets: list of (C,H,W) float32 CUDA tensors; params: list of SMoEParams
     (each image's own tensors, updated in place); iters: per-image run length
     (int or list); lr = (mu0, mu1, chol, ea, eW[, pi]) or one tuple per image
-    (pi: the rate of the gate weights log pi_k, for parameters that carry them);
+    (pi: the rate of the gate weights log pi_k, for parameters that carry them;
+    default: synth.fit_rates of each image, the paper's rates with the centre
+    rate in pixels);
     rbf: fit the unnormalised RBF sum of Eq. 1 instead of the softmax gates;
     persistent: run the fused tile kernel as one persistent grid;
     deterministic: per-pair gradient partials added in a fixed order (a fit
@@ -32,7 +34,7 @@ class FitBatch:
     are neighbours).  The batch's parameter tensors then hold the kernels in
     that order; params_of() returns them in the caller's order."""
 
-    def __init__(self, targets, params, iters, lr=(1e-2, 1e-5, 1e-3, 1e-3, 1e-3), tile=16,
+    def __init__(self, targets, params, iters, lr=None, tile=16,
                  qmax=9.0, b1=0.9, b2=0.999, eps=1e-8, hist=None, pair_slack=1.5,
                  persistent=False, pair_cap=None, moments=None, steps=None,
                  deterministic=False, device="cuda", rbf=False, reorder_every=None):
@@ -51,7 +53,11 @@ class FitBatch:
         self.deterministic = bool(deterministic)
         self.targets = [t.contiguous() for t in targets]
         self.iters = [iters] * self.B if np.isscalar(iters) else list(iters)
-        self.lr = [lr] * self.B if np.isscalar(lr[0]) else list(lr)
+        if lr is None:
+            from .synth import fit_rates
+            self.lr = [fit_rates(t.shape[2], t.shape[1]) for t in self.targets]
+        else:
+            self.lr = [lr] * self.B if np.isscalar(lr[0]) else list(lr)
         self.params = list(params)
         self.Ks = [p.K for p in params]
         if moments is None:
@@ -119,18 +125,23 @@ class FitBatch:
         self.graph = None
         self._reorder_graph = None
 
-    def params_of(self, b):
+    def params_of(self, b, out=None, stream=None):
         """Image b's parameters in the caller's kernel order: the batch's own
         tensors, or (after reordering) a copy scattered back through the
-        order map by smoe_scatter_params."""
+        order map by smoe_scatter_params (into ``out`` when given, an
+        SMoEParams of the same shape, else into new tensors)."""
         if self.order is None:
+            if out is not None:
+                for d, s_ in zip(out.tensors(), self.params[b].tensors()):
+                    d.copy_(s_)
+                return out
             return self.params[b]
         src = self.params[b]
-        dst = src.zeros_like()
+        dst = src.zeros_like() if out is None else out
         if src.K:
             idx = self.order[self.k_off[b]:self.k_off[b] + src.K]
             check(_lib.load().smoe_scatter_params(ctypes.byref(src.c()), _ptr(idx), self.k_off[b],
-                                                  self.C, ctypes.byref(dst.c()), _stream(None)),
+                                                  self.C, ctypes.byref(dst.c()), _stream(stream)),
                   "smoe_scatter_params")
         return dst
 
@@ -182,6 +193,27 @@ class FitBatch:
         check(_lib.load().smoe_fit_phase(ctypes.byref(self._batch), self._imgs, self.pair_cap,
                                          _ptr(self.ws), self.ws.numel(), phase,
                                          _ptr(self.status), _stream(stream)), "smoe_fit_phase")
+
+    def gradients(self, stream=None, with_pi=None):
+        """The gradients this iteration would apply (smoe_fit_gradients):
+        bins, runs the fused forward / MSE / backward launch and reads out
+        every kernel's finalized dL/dtheta without stepping Adam.  Returns one
+        SMoEParams per image, rows in the batch's kernel order (the caller's
+        order unless the batch has been re-sorted; see params_of).  with_pi:
+        also return dL/dlogpi (default: when the parameters carry logpi)."""
+        K = sum(self.Ks)
+        if with_pi is None:
+            with_pi = self.params[0].logpi is not None
+        g = SMoEParams.zeros(K, self.C, self.linear, device=self.device, pi=with_pi)
+        check(_lib.load().smoe_fit_gradients(ctypes.byref(self._batch), self._imgs, self.pair_cap,
+                                             _ptr(self.ws), self.ws.numel(), ctypes.byref(g.c()),
+                                             _ptr(self.status), _stream(stream)),
+              "smoe_fit_gradients")
+        out = []
+        for b in range(self.B):
+            a, n = self.k_off[b], self.Ks[b]
+            out.append(SMoEParams(*(None if t is None else t[a:a + n] for t in g.slots())))
+        return out
 
     def capture(self, n_iters=1):
         """Capture n_iters iterations into a CUDA graph."""

@@ -104,7 +104,7 @@ class _Slot:
 class Server:
     """Continuous-batching server on one GPU (see the module docstring)."""
 
-    def __init__(self, hbm_budget, tile=16, lr=synth.PAPER_LR, chunk=25, graphs=True,
+    def __init__(self, hbm_budget, tile=16, lr=None, chunk=25, graphs=True,
                  persistent=False, qmax=9.0, deterministic=True, max_pixels=None):
         """max_pixels: cap on the pixels in flight (image pixels x models over
         the admitted fits); beyond the point where one batch fills the GPU,
@@ -307,7 +307,7 @@ class Server:
         return results
 
 
-def serve_plain(requests, tile=16, lr=synth.PAPER_LR, qmax=9.0, realtime=True, graphs=True,
+def serve_plain(requests, tile=16, lr=None, qmax=9.0, realtime=True, graphs=True,
                 deterministic=True):
     """Baseline: one request at a time in arrival order, one image per launch."""
     reqs = sorted(requests, key=lambda r: r.arrival)

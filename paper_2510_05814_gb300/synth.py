@@ -227,7 +227,21 @@ class Workload:
     extra: dict = field(default_factory=dict)
 
 
+# The Adam rates printed in Sec. VI-B: centres 0.01 decaying exponentially to
+# 0.00001, covariance factor 0.001, experts 0.001 (mu0, mu1, chol, ea, eW).
 PAPER_LR = (1e-2, 1e-5, 1e-3, 1e-3, 1e-3)
+
+
+def fit_rates(W, H, lr_pi=None):
+    """The Sec. VI-B rates in the units of the fit API for a W x H image:
+    the centre rates are read in pixels per step (0.01 px decaying to
+    1e-5 px, the same on every raster size), and the API's centres are
+    normalised (pixel = mu * (W, H)), so they are divided by the longer
+    side; the Cholesky factor and the experts take the printed 0.001.
+    lr_pi, when given, is appended as the rate of the gate weights."""
+    s = 1.0 / max(W, H)
+    lr = (PAPER_LR[0] * s, PAPER_LR[1] * s) + PAPER_LR[2:]
+    return lr + (lr_pi,) if lr_pi is not None else lr
 
 
 def plain_gray_128(seed=1):

@@ -55,3 +55,29 @@ def test_argument_errors_are_synchronous():
                       ctypes.c_void_p(4096), ctypes.c_void_p(8192), 100, ctypes.c_void_p(16),
                       ctypes.c_void_p(32), None)
     assert st == _lib.SMOE_ERR_ARG
+
+
+def test_static_render_and_sharpen_refuse_cutoffs_beyond_the_fp32_range():
+    """q_max above 174 (an included pair's gate would flush to 0) is refused
+    by the no-allocation render as by smoe_render, and smoe_sharpen refuses a
+    factor whose q_max' = q_max f^2 exceeds it; both answer on the host."""
+    from paper_2510_05814_gb300 import build, _lib
+    build.build()
+    lib = _lib.load()
+    wide = _lib.Desc(64, 64, 3, 16, 0, 200.0, 1.0, 0)
+    p = _lib.Params(10, 256, 512, 768, None, None)
+    st = lib.smoe_render_static(ctypes.byref(wide), ctypes.byref(p), ctypes.c_void_p(4096),
+                                ctypes.c_void_p(8192), ctypes.c_void_p(16), None)
+    assert st == _lib.SMOE_ERR_ARG
+    q = ctypes.c_float(-1.0)
+    st = lib.smoe_sharpen(ctypes.c_void_p(256), ctypes.c_void_p(512), 10, 5.0, 9.0,
+                          ctypes.byref(q), None)
+    assert st == _lib.SMOE_ERR_ARG and q.value == -1.0
+    st = lib.smoe_sharpen(ctypes.c_void_p(256), ctypes.c_void_p(512), 10, 2.0, 9.0,
+                          None, None)
+    assert st == _lib.SMOE_ERR_ARG
+    # K = 0 launches nothing: the cutoff comes back from the host
+    st = lib.smoe_sharpen(None, None, 0, 3.3, 9.0, ctypes.byref(q), None)
+    assert st == _lib.SMOE_OK
+    import numpy as np
+    assert q.value == float(np.float32(9.0) * (np.float32(3.3) * np.float32(3.3)))

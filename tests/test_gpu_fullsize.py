@@ -144,6 +144,42 @@ def test_autograd_64_parameters_vs_oracle_and_central_differences(wl):
     assert checked_fd >= 12
 
 
+def test_fullsize_fit_gradients_sampled(wl):
+    """The gradients of the fused fit path (fused forward / MSE / backward
+    tile launch and the Adam launch's finalize, read out by
+    smoe_fit_gradients) at the full 2048^2 workload in the bench's launch
+    configuration (T = 16, one CTA per tile, float atomics): every parameter
+    of 48 random kernels against the oracle's analytic MSE gradient,
+    |g - g_ref| <= 1e-4 max(|g_ref|, 1e-2 x the sum of term magnitudes)."""
+    from paper_2510_05814_gb300.fit import FitBatch
+    C, H, W = wl.target.shape
+    P = wl.params
+    fb = FitBatch([torch.tensor(wl.target, device="cuda")], [api.SMoEParams.from_numpy(P)], 2,
+                  lr=synth.PAPER_LR, tile=T)
+    g = fb.gradients()[0]
+    assert fb.status_code() == 0
+    got = [x.cpu().numpy() for x in g.tensors()]
+    full = om.Model(W, H, C, P.mu, P.chol, P.ea, P.eW, tile=T)
+    tx = (W + T - 1) // T
+    rng = np.random.default_rng(103)
+    checked = 0
+    for k in rng.choice(P.K, 48, replace=False):
+        (x0, y0, x1, y1), cnt = om.rect(full, int(k))
+        if cnt == 0:
+            continue
+        tiles = np.array([ty * tx + t for ty in range(y0, y1 + 1) for t in range(x0, x1 + 1)])
+        m, ids = sub_model(P, W, H, tiles, extra=[k])
+        pos = int(np.searchsorted(ids, k))
+        rg, rt = om.backward(m, target=wl.target, kernels=[pos], with_scale=True)
+        for gi, name in enumerate(["mu", "chol", "ea", "eW"]):
+            ref, terms = rg[gi][0].ravel(), rt[gi][0].ravel()
+            a = got[gi][k].ravel()
+            den = np.maximum(np.abs(ref), 1e-2 * terms)
+            assert np.all(np.abs(a - ref) <= 1e-4 * den), (int(k), name, a, ref, terms)
+        checked += 1
+    assert checked >= 40
+
+
 def test_ragged_batch_fullsize_losses():
     """Config 4 at full size: the 64 ragged images (128x96 .. 1920x1080,
     K = pixels/16, 35 M pixels) as one fit batch.  After one fused iteration

@@ -66,6 +66,11 @@ def test_static_render_limits():
     yb = torch.zeros(1, device="cuda")
     assert static_render(big, api.SMoEParams.from_numpy(model(4, 64, 64, 64, False)), yb, yb,
                          status) == _lib.SMOE_ERR_WORKSPACE
+    # a cutoff beyond the largest one every entry point accepts: refused
+    # (smoe_render's raster check, SMOE_ERR_ARG)
+    wide = api.RasterDesc(64, 64, 3, 16, False, qmax=200.0)
+    small = api.SMoEParams.from_numpy(model(6, 64, 64, 64, False))
+    assert static_render(wide, small, y, inv, status) == _lib.SMOE_ERR_ARG
     # too many pairs: reported on the device, image left untouched
     p = api.SMoEParams.from_numpy(model(5, 512, 512, 32768, False, 40.0))
     desc = api.RasterDesc(512, 512, 3, 8, False)
