@@ -58,9 +58,9 @@ REORDER_KERNELS = 15
 # operations (FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) thread
 # instructions); valid only while render.cu's code (comments and whitespace
 # aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "023a846244615376ce0e0d757481649c77f809707901515cfd6718cc83e15ca3",
-       "bytes_per_launch": 103.523072e6, "fma_pipe_active": 0.624, "issue_active": 0.613,
-       "xu_active": 0.129, "fp32_lane_ops": 15.535109205e9}
+NCU = {"render_cu_code_sha256": "adace238d679bfb7c5ccdf8d64aa3e5ddfc94541addbd0e68aed237dbf234c9a",
+       "bytes_per_launch": 103.190784e6, "fma_pipe_active": 0.609, "issue_active": 0.621,
+       "xu_active": 0.135, "fp32_lane_ops": 14.632636181e9}
 
 def issue_rates():
     """Measured lane operations per clock per SM of ex2 / FFMA / packed

@@ -46,7 +46,10 @@ namespace smoe {
 
 namespace {
 
-constexpr int kNW = 4;                // warps per CTA
+#ifndef SMOE_NW
+#define SMOE_NW 4
+#endif
+constexpr int kNW = SMOE_NW;          // warps per CTA
 constexpr int kThreads = kNW * 32;
 // Resident CTAs per SM that the register budget targets, and the chunk of a
 // tile's list staged in shared memory at once (tiles of 8 and 16 pixels).
@@ -59,7 +62,15 @@ constexpr int kThreads = kNW * 32;
 #ifndef SMOE_FWD_UNROLL
 #define SMOE_FWD_UNROLL 4
 #endif
+// Backward: rows of the tile one warp step covers (a group of 32 / rows
+// kernels, each on that many rows at once).
+#ifndef SMOE_BWD_ROWS
+#define SMOE_BWD_ROWS 2
+#endif
+
 constexpr int kMinBlocks = SMOE_MIN_BLOCKS;
+constexpr int kBwdRows = SMOE_BWD_ROWS;
+static_assert(kBwdRows == 1 || kBwdRows == 2 || kBwdRows == 4, "rows per backward step");
 // The forward-only kernels (render, fused mean) need fewer registers than
 // the backward: one more resident CTA per SM measured faster for them.
 #ifndef SMOE_MIN_BLOCKS_FWD
@@ -160,6 +171,13 @@ __device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const T
         const float y0f = (float)ti.y0 + 0.5f;
         const float xl = (float)ti.x0 + 0.5f;              // first and last column centres
         const float xr = (float)ti.x0 + ((float)T - 0.5f);
+        // least q32 of a row over the columns between two of them (exact
+        // where z0 keeps one sign there, else the u test)
+        auto row_min = [](float zl, float zr, float u) {
+            const float zm = fminf(fabsf(zl), fabsf(zr));
+            const bool one_sign = (zl >= 0.0f) == (zr >= 0.0f);
+            return one_sign ? __fmaf_rn(zm, zm, u) : u;
+        };
         for (int base = threadIdx.x & ~31; base < LPK * nc; base += kThreads) {
             const int i = base + lane;
             const int j = i < LPK * nc ? i / LPK : 0;
@@ -175,10 +193,7 @@ __device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const T
                 const float z1 = __fmul_rn(c, dy);
                 const float u = __fmul_rn(z1, z1);
                 const float zl = __fmaf_rn(a, dxl, t), zr = __fmaf_rn(a, dxr, t);
-                const float zm = fminf(fabsf(zl), fabsf(zr));
-                const bool one_sign = (zl >= 0.0f) == (zr >= 0.0f);
-                const float qm = one_sign ? __fmaf_rn(zm, zm, u) : u;
-                m |= (qm <= g.qmax ? 1u : 0u) << rr;
+                m |= (row_min(zl, zr, u) <= g.qmax ? 1u : 0u) << rr;
             }
             m <<= r0;
 #pragma unroll
@@ -190,6 +205,18 @@ __device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const T
 }
 
 // ---------------------------------------------------------------- forward
+
+// Pixel (row, col) of the lane's pair for band slot bi, and whether this warp
+// finalises it (T = 8: only warp 0 after the reduction).
+template <int C, int T>
+__device__ __forceinline__ bool lane_pixels(int bi, int &row, int &col) {
+    using G = Geom<C, T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int band = G::KSPLIT > 1 ? 0 : warp + bi * kNW;
+    row = band * G::BROWS + lane / G::LROW;
+    col = 2 * (lane % G::LROW);
+    return G::KSPLIT == 1 || warp == 0;
+}
 
 // One kernel's contribution to a lane's two pixels (row y0, columns x2).
 template <int C, bool LIN>
@@ -311,8 +338,8 @@ __device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const Tile
 #pragma unroll
         for (int bi = 0; bi < G::BPW; ++bi) {
             const int band = G::KSPLIT > 1 ? 0 : warp + bi * kNW;
-            const int row = band * G::BROWS + lane / G::LROW;
-            const int col = 2 * (lane % G::LROW);
+            int row, col;
+            lane_pixels<C, T>(bi, row, col);
             const uint32_t bm = (G::BROWS >= 32 ? 0xffffffffu : ((1u << G::BROWS) - 1u))
                                 << (band * G::BROWS);
             fwd_band<C, LIN, T>(g, ti, sm, nc, split, G::KSPLIT, bm, row, col, Dv[bi], Nv[bi]);
@@ -346,18 +373,6 @@ __device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const Tile
             }
         }
     }
-}
-
-// Pixel (row, col) of the lane's pair for band slot bi, and whether this warp
-// finalises it (T = 8: only warp 0 after the reduction).
-template <int C, int T>
-__device__ __forceinline__ bool lane_pixels(int bi, int &row, int &col) {
-    using G = Geom<C, T>;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int band = G::KSPLIT > 1 ? 0 : warp + bi * kNW;
-    row = band * G::BROWS + lane / G::LROW;
-    col = 2 * (lane % G::LROW);
-    return G::KSPLIT == 1 || warp == 0;
 }
 
 template <int C, bool LIN, int T>
@@ -531,10 +546,18 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
         }
         __syncthreads();
         const int n_live = sm.boff[NB];
-        // One 32-kernel group: every lane walks its kernel over the rows in
-        // `rowsel` of the union of the group's row masks.
-        auto group = [&](int grp, uint32_t rowsel) {
-            const int idx = grp * 32 + lane;
+        // One group of KG = 32 / RPS kernels.  The rows it walks are the
+        // selected rows base + stride i (all rows, or every fourth when the
+        // warps share a group), taken RPS at a time: lane l works on kernel
+        // grp KG + l % KG and, in block b, on selected row RPS b + l / KG.  A
+        // block is skipped when no kernel of the group has a live row in it.
+        // Which lane takes a row depends on the row alone, so a kernel's sums
+        // do not depend on the other kernels of its group.
+        constexpr int RPS = kBwdRows;
+        constexpr int KG = 32 / RPS;
+        auto group = [&](int grp, int base, int stride) {
+            const int sub = lane / KG;
+            const int idx = grp * KG + (lane % KG);
             const bool valid = idx < n_live;
             const int j = valid ? sm.order[idx] : 0;
             const uint32_t m = valid ? sm.mask[j] : 0u;
@@ -556,11 +579,29 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             BwdAcc<C, LIN> acc;
             acc.zero();
             const float2 nmx = f2(-mx), a2 = f2(a), lp2 = f2(v[5]);
-            uint32_t rows = __reduce_or_sync(0xffffffffu, m) & rowsel;
-            while (rows) {
-                const int r = __ffs(rows) - 1;
-                rows &= rows - 1;
-                const float qm = (m >> r) & 1u ? qmax : -1.0f;   // other lanes add zero
+            // blocks of RPS selected rows that hold a live row of the group
+            const uint32_t um = __reduce_or_sync(0xffffffffu, m);
+            const int nsel = T / stride;
+            uint32_t blocks = 0;
+#pragma unroll
+            for (int bb = 0; bb < (T + RPS - 1) / RPS; ++bb) {
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < RPS; ++q) {
+                    const int i = RPS * bb + q;
+                    if (i < nsel) any |= ((um >> (base + stride * i)) & 1u) != 0;
+                }
+                blocks |= (any ? 1u : 0u) << bb;
+            }
+            const uint32_t msel = m;
+            while (blocks) {
+                const int bb = __ffs(blocks) - 1;
+                blocks &= blocks - 1;
+                const int i = RPS * bb + sub;
+                const bool in = i < nsel;
+                const int r = in ? base + stride * i : 0;
+                // lanes whose kernel has no live pixel in row r add zero
+                const float qm = in && ((msel >> r) & 1u) ? qmax : -1.0f;
                 const float dy = __fsub_rn(__fadd_rn(y0f, (float)r), my);
                 const float t = __fmul_rn(b, dy);
                 const float z1 = __fmul_rn(c, dy);
@@ -634,7 +675,16 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
                     }
                 }
             }
-            if (m & rowsel) {
+            // the RPS lanes of each kernel add their sums (a fixed order)
+#pragma unroll
+            for (int o = KG; o < 32; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < R::GS; ++q) acc.v[q] += __shfl_xor_sync(0xffffffffu, acc.v[q], o);
+            // every stride-th row from base (stride 1, 2, 4 or 8)
+            const uint32_t every = stride == 1 ? 0xffffffffu : stride == 2 ? 0x55555555u
+                                 : stride == 4 ? 0x11111111u : 0x01010101u;
+            const uint32_t rowsel = every << base;
+            if (sub == 0 && (m & rowsel)) {
                 if (w.part) {        // deterministic: this pair's own slot
                     float4 *dst = reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS);
 #pragma unroll
@@ -654,10 +704,10 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
         // n_groups mod kNW groups of the last round are shared by all warps,
         // each taking the rows r = warp (mod kNW) and adding its own partial
         // sums (the deterministic mode keeps whole groups: one writer per pair).
-        const int n_groups = (n_live + 31) >> 5;
+        const int n_groups = (n_live + KG - 1) / KG;
         const int whole = w.part ? n_groups : n_groups - n_groups % kNW;
-        for (int grp = warp; grp < whole; grp += kNW) group(grp, 0xffffffffu);
-        for (int grp = whole; grp < n_groups; ++grp) group(grp, 0x11111111u << warp);
+        for (int grp = warp; grp < whole; grp += kNW) group(grp, 0, 1);
+        for (int grp = whole; grp < n_groups; ++grp) group(grp, warp, kNW);
         if (w.part) {                // pairs whose kernel misses every row add zero
             for (int i = threadIdx.x; i < nc * (R::GS / 4); i += kThreads) {
                 const int j = i / (R::GS / 4), q = i - j * (R::GS / 4);
