@@ -770,9 +770,28 @@ __device__ __forceinline__ void fit_tile_body(const Geo &g, const Bufs &w, int64
     const ImgDev &im = img_of(g, ti.b);
     const int32_t it = step ? step[ti.b] : 0;
     if (it >= im.iters) return;                      // this image has finished its run
+    const int64_t HW = (int64_t)ti.W * ti.H;
+    // With one band per warp (T <= 16) the lane's target values are loaded
+    // before the forward, so that they arrive while it runs (0 outside the
+    // image, where they are not read); with more bands they would hold too
+    // many registers and are read after it.
+    constexpr bool kEarly = G::BPW == 1;
+    float tg[G::BPW][2][C];
+#pragma unroll
+    for (int bi = 0; bi < (kEarly ? G::BPW : 0); ++bi) {
+        int row, col;
+        const bool mine = lane_pixels<C, T>(bi, row, col);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xi = ti.x0 + col + h, yi = ti.y0 + row;
+            const bool in = mine && xi < ti.W && yi < ti.H;
+            const int64_t o = (int64_t)yi * ti.W + xi;
+#pragma unroll
+            for (int ch = 0; ch < C; ++ch) tg[bi][h][ch] = in ? __ldg(im.target + ch * HW + o) : 0.0f;
+        }
+    }
     float2 Dv[G::BPW], Nv[G::BPW][C];
     fwd_tile<C, LIN, T>(g, w, ti, sm, Dv, Nv);
-    const int64_t HW = (int64_t)ti.W * ti.H;
     const float norm = 2.0f / ((float)C * (float)HW);
     float se = 0.0f;                                 // this thread's <= 2 C squared errors per band
 #pragma unroll
@@ -794,7 +813,7 @@ __device__ __forceinline__ void fit_tile_body(const Geo &g, const Bufs &w, int64
 #pragma unroll
                 for (int ch = 0; ch < C; ++ch) {
                     const float yv = (h ? Nv[bi][ch].y : Nv[bi][ch].x) * inv;
-                    const float d = yv - im.target[ch * HW + o];
+                    const float d = yv - (kEarly ? tg[bi][h][ch] : im.target[ch * HW + o]);
                     se = fmaf(d, d, se);
                     H[h][ch] = inv * (norm * d);
                     if (!g.rbf) nHy[h] = fmaf(-H[h][ch], yv, nHy[h]);

@@ -78,7 +78,7 @@ def fit_bytes(C, H, W, K):
     """Device bytes a fit slot holds: parameters + two Adam moments + target +
     its share of the fit workspace (records, sums, boxes, lists)."""
     n_param = K * (5 + 3 * C)
-    pairs = 10 * K
+    pairs = 40 * K          # ~13 (tile, kernel) pairs per kernel at T = 16, 3x headroom
     return 4 * (3 * n_param + C * H * W) + K * (64 + 64 + 16) + 12 * pairs
 
 
@@ -143,7 +143,7 @@ class Server:
                 slots.append(s)
         return slots
 
-    def _form_batch(self, slots, slack=1.5):
+    def _form_batch(self, slots, slack=3.0):
         cap = int(slack * sum(s.pairs for s in slots)) + 4096
         with torch.cuda.stream(self.fit_stream):
             self.batch = FitBatch([s.target for s in slots], [s.params for s in slots],
@@ -326,12 +326,11 @@ def serve_plain(requests, tile=16, lr=None, qmax=9.0, realtime=True, graphs=True
             ps, losses = [], []
             for p in denoise.init_models(r.image, r.models, K, r.sigma, True, seed=r.seed):
                 fb = FitBatch([tgt], [p], r.iters, lr=lr, tile=tile, qmax=qmax,
-                              deterministic=deterministic)
-                if graphs:
-                    fb.capture(r.iters)
-                    fb.graph.replay()
-                else:
-                    fb.launch(r.iters)
+                              deterministic=deterministic, pair_slack=3.0)
+                # graph replays of 25 iterations; a pair-buffer overflow (the
+                # lists grow as kernels widen) grows the buffer and resumes
+                fb.run(r.iters, graph_iters=min(25, r.iters) if graphs else None,
+                       check_every=r.iters)
                 st = fb.status_code()
                 if st != 0:
                     raise RuntimeError(f"fit status {st}")
