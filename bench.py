@@ -58,9 +58,9 @@ REORDER_KERNELS = 15
 # operations (FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) thread
 # instructions); valid only while render.cu's code (comments and whitespace
 # aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "adace238d679bfb7c5ccdf8d64aa3e5ddfc94541addbd0e68aed237dbf234c9a",
-       "bytes_per_launch": 103.190784e6, "fma_pipe_active": 0.609, "issue_active": 0.621,
-       "xu_active": 0.135, "fp32_lane_ops": 14.632636181e9}
+NCU = {"render_cu_code_sha256": "5b9c1c57ba09f0706eaeebc3c0ea6da0e03c664e26e1d3e4697cc4eb4ac3700e",
+       "bytes_per_launch": 103.111424e6, "fma_pipe_active": 0.614, "issue_active": 0.627,
+       "xu_active": 0.137, "fp32_lane_ops": 14.632777877e9}
 
 def issue_rates():
     """Measured lane operations per clock per SM of ex2 / FFMA / packed
@@ -739,6 +739,54 @@ def main():
     return run_fit(args)
 
 
+def roofline_fields(inrange, listed, tile_s, rates, sms, fallback_mhz, ncu):
+    """The line's roofline objects for the fused tile kernel: `roofline` (the
+    FP32 pipe on the method's in-range work), `roofline_ex2` (in-range and
+    listed pairs) and `fp32_executed` (ncu-counted work, or None).
+    inrange / listed: pairs of one launch; tile_s: its mean CUDA-event time;
+    rates: the live issue-rate measurements (dicts with ex2, ffma and
+    clock_mhz), possibly empty; ncu: the profiled figures or None."""
+    clk = statistics.mean(r["clock_mhz"] for r in rates) if rates else fallback_mhz
+    mufu = statistics.mean(r["ex2"] for r in rates) if rates else MUFU_PER_CLK_PER_SM
+    ffma = statistics.mean(r["ffma"] for r in rates) if rates else 128.0
+    ex2_peak = mufu * sms * clk * 1e6                              # ex2 / s
+    fma_peak = ffma * sms * clk * 1e6                              # FP32 lane-ops / s
+    fma_alg = FP32_OPS_PER_PAIR * inrange                          # per launch
+    basis = (f"{sms} SMs x {clk:.0f} MHz (SM clock measured live by libsmoe_rates before "
+             "and after the timed region)" if rates else f"{sms} SMs x {clk:.0f} MHz (fallback)")
+    ex2 = lambda pairs: {"achieved": 2.0 * pairs / tile_s / 1e9, "peak": ex2_peak / 1e9,
+                         "unit": "Gex2/s", "frac": 2.0 * pairs / tile_s / ex2_peak}
+    out = {
+        "roofline": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
+                     "achieved": fma_alg / tile_s / 1e12, "peak": fma_peak / 1e12,
+                     "unit": "T FP32 lane-ops/s", "frac": fma_alg / tile_s / fma_peak,
+                     "traffic": ncu["bytes_per_launch"] if ncu else None,
+                     "per_unit": {"unit": "in-range (q <= q_max) fwd+bwd pixel-kernel pair",
+                                  "fp32_lane_ops": FP32_OPS_PER_PAIR,
+                                  "units_per_launch": int(inrange),
+                                  "launch_ms": tile_s * 1e3},
+                     "peak_basis": f"{ffma:.1f} FFMA lanes/clk/SM (libsmoe_rates, live) x "
+                                   + basis,
+                     "issue_rates_per_clk_per_sm": list(rates)},
+        "roofline_ex2": {
+            "in_range": dict(ex2(inrange), basis="2 ex2 per in-range fwd+bwd pair"),
+            "listed": dict(ex2(listed), basis="2 ex2 per listed pair (sum over tiles of pixels "
+                                              "x list length): the metric's pair count"),
+            "peak_basis": f"{mufu:.1f} ex2 lanes/clk/SM (libsmoe_rates, live) x " + basis},
+        "fp32_executed": None,
+    }
+    if ncu and ncu.get("fp32_lane_ops"):
+        out["fp32_executed"] = {
+            "lane_ops_per_launch": ncu["fp32_lane_ops"],
+            "per_in_range_pair": ncu["fp32_lane_ops"] / inrange,
+            "achieved": ncu["fp32_lane_ops"] / tile_s / 1e12, "unit": "T FP32 lane-ops/s",
+            "frac": ncu["fp32_lane_ops"] / tile_s / fma_peak,
+            "source": "ncu sass thread-instruction counts of one launch (FFMA + FADD + "
+                      "FMUL + 2 x (FFMA2 + FADD2 + FMUL2)), profiles/",
+            "pipes": {k: ncu[k] for k in ("fma_pipe_active", "issue_active", "xu_active")}}
+    return out
+
+
 def run_fit(args):
     import numpy as np
     # host inputs first: the pool is spawned before this process uses the GPU
@@ -917,23 +965,13 @@ def run_fit(args):
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     rl = [r for r in (rates0, rates1) if r]
-    # the SM clock measured live by the issue-rate kernels just before and
-    # just after the timed region (the 200 ms nvidia-smi poll sees too few
-    # samples of a short region)
-    clk_mhz = statistics.mean(r["clock_mhz"] for r in rl) if rl else (clocks.get("sm_mhz") or 2070.0)
-    mufu = statistics.mean(r["ex2"] for r in rl) if rl else MUFU_PER_CLK_PER_SM
-    ffma = statistics.mean(r["ffma"] for r in rl) if rl else 128.0
-    ex2_peak = mufu * sms * clk_mhz * 1e6                          # ex2 / s
-    fma_peak = ffma * sms * clk_mhz * 1e6                          # FP32 lane-ops / s
     tile_s = statistics.mean(tile_ms) / 1e3
-    fma_alg = FP32_OPS_PER_PAIR * inrange_step                     # per launch
     ncu = None
     if NCU["render_cu_code_sha256"] and NCU["render_cu_code_sha256"] == code_sha256(
             os.path.join(ROOT, "paper_2510_05814_gb300", "csrc", "render.cu")):
         ncu = NCU
-    traffic = ncu["bytes_per_launch"] if ncu else None
-    basis = (f"{sms} SMs x {clk_mhz:.0f} MHz (SM clock measured live by libsmoe_rates before "
-             "and after the timed region)")
+    roof = roofline_fields(inrange_step, pairs_step, tile_s, rl, sms,
+                           clocks.get("sm_mhz") or 2070.0, ncu)
 
     cpu = cpu_binned = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -964,37 +1002,8 @@ def run_fit(args):
                        "pairs_per_step": int(pairs_step), "list_pairs": int(lists1),
                        "in_range_pairs_per_step": int(inrange_step)},
             # the binding resource of the fused tile kernel: the FP32 pipe, on
-            # the method's work (pairs inside the cutoff)
-            "roofline": {"bound": "alu", "kernel": "k_fit_tile (fused fwd+MSE+bwd)",
-                         "achieved": fma_alg / tile_s / 1e12, "peak": fma_peak / 1e12,
-                         "unit": "T FP32 lane-ops/s", "frac": fma_alg / tile_s / fma_peak,
-                         "traffic": traffic,
-                         "per_unit": {"unit": "in-range (q <= q_max) fwd+bwd pixel-kernel pair",
-                                      "fp32_lane_ops": FP32_OPS_PER_PAIR,
-                                      "units_per_launch": int(inrange_step),
-                                      "launch_ms": tile_s * 1e3},
-                         "peak_basis": f"{ffma:.1f} FFMA lanes/clk/SM (libsmoe_rates, live) x "
-                                       + basis,
-                         "issue_rates_per_clk_per_sm": rl},
-            "roofline_ex2": {
-                "in_range": {"achieved": 2.0 * inrange_step / tile_s / 1e9,
-                             "peak": ex2_peak / 1e9, "unit": "Gex2/s",
-                             "frac": 2.0 * inrange_step / tile_s / ex2_peak,
-                             "basis": "2 ex2 per in-range fwd+bwd pair"},
-                "listed": {"achieved": 2.0 * pairs_step / tile_s / 1e9,
-                           "peak": ex2_peak / 1e9, "unit": "Gex2/s",
-                           "frac": 2.0 * pairs_step / tile_s / ex2_peak,
-                           "basis": "2 ex2 per listed pair (sum over tiles of pixels x list "
-                                    "length): the metric's pair count"},
-                "peak_basis": f"{mufu:.1f} ex2 lanes/clk/SM (libsmoe_rates, live) x " + basis},
-            "fp32_executed": None if ncu is None or not ncu.get("fp32_lane_ops") else {
-                "lane_ops_per_launch": ncu["fp32_lane_ops"],
-                "per_in_range_pair": ncu["fp32_lane_ops"] / inrange_step,
-                "achieved": ncu["fp32_lane_ops"] / tile_s / 1e12, "unit": "T FP32 lane-ops/s",
-                "frac": ncu["fp32_lane_ops"] / tile_s / fma_peak,
-                "source": "ncu sass thread-instruction counts of one launch (FFMA + FADD + "
-                          "FMUL + 2 x (FFMA2 + FADD2 + FMUL2)), profiles/",
-                "pipes": {k: ncu[k] for k in ("fma_pipe_active", "issue_active", "xu_active")}},
+            # the method's work (pairs inside the cutoff); ex2 and the executed work beside it
+            **roof,
             "value_fwd_bwd_only": pairs_step / tile_s / 1e9,
             # pairs with q <= q_max (the ones that contribute) per second of the
             # fused tile kernel, and their share of the listed pairs
@@ -1007,6 +1016,12 @@ def run_fit(args):
                           "how": "the same step launched phase by phase (no graph), "
                                  "CUDA events between the phases"},
             "fit_iters_per_s": args.steps / tot_s,
+            # the fit wall-time at 2048^2: a fresh fit to the stated PSNR, and the
+            # PSNR the paper's 10000 iterations reach
+            "fit_wall_s_to_psnr": None if fit_leg is None else {
+                "target_psnr_db": fit_leg["target_psnr_db"], "s": fit_leg["s_to_target"],
+                "iters": fit_leg["iters_to_target"], "fit_s": fit_leg["device_s"],
+                "fit_iters": fit_leg["iters"], "psnr_final_db": fit_leg["psnr_final_db"]},
             "fit_to_psnr": fit_leg,
             "batched_vs_plain": batched,
             "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
