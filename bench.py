@@ -301,11 +301,13 @@ def run_batched(args):
     # FitBatch.run: graph replays with the re-sort every `chunk` iterations; a
     # pair-buffer overflow (the lists grow as kernels widen) grows the buffer
     # and resumes, inside the timed region, in both arms
+    cap0 = fb.pair_cap
     e0.record()
     fb.run(n, graph_iters=chunk)
     e1.record()
     torch.cuda.synchronize()
     assert fb.status_code() == 0
+    grown = {"batched": int(fb.pair_cap != cap0), "plain": 0}
     t_batched = e0.elapsed_time(e1) / 1e3
     # plain: each image alone, one image per launch, same iterations
     t_plain = 0.0
@@ -316,6 +318,7 @@ def run_batched(args):
         one.capture(chunk)
         one.reorder()
         torch.cuda.synchronize()
+        cap0 = one.pair_cap
         e0.record()
         one.run(n, graph_iters=chunk)
         e1.record()
@@ -323,6 +326,7 @@ def run_batched(args):
         t_plain += e0.elapsed_time(e1) / 1e3
         lat_plain.append(t_plain)
         assert one.status_code() == 0
+        grown["plain"] += int(one.pair_cap != cap0)
         C, H, W = targets[b].shape
         yb, _, _ = api.render(fb.params_of(b), W, H, tile=tr.tile)
         yp, _, _ = api.render(one.params_of(0), W, H, tile=tr.tile)
@@ -343,7 +347,7 @@ def run_batched(args):
         "mode": "batched", "images": len(targets), "iters": n,
         "pixels": int(sum(t.shape[1] * t.shape[2] for t in targets)),
         "kernels": int(sum(p.K for p in params)), "pairs_per_iter": int(pairs),
-        "reorder_every": chunk,
+        "reorder_every": chunk, "pair_buffers_grown": grown,
         "autotune": {"tile": tr.tile, "persistent": tr.persistent,
                      "table_ms_per_iter": [[a, bool(b_), c] for a, b_, _, c in tr.table]},
         "batched": {"s": t_batched, "ms_per_iter": 1e3 * t_batched / n,
@@ -704,6 +708,9 @@ def main():
     ap.add_argument("--batched-images", type=int, default=64,
                     help="images of the batched-vs-plain leg (0: skip)")
     ap.add_argument("--batched-iters", type=int, default=25)
+    ap.add_argument("--serve-fits", type=int, default=12,
+                    help="fit requests of the serving leg (as many renders; 0: skip)")
+    ap.add_argument("--serve-iters", type=int, default=200)
     ap.add_argument("--mode", default="fit",
                     choices=["fit", "batched", "serve", "denoise", "quality"],
                     help="fit: the 2048^2 fit step (default); batched: 64 ragged images; "
@@ -737,6 +744,39 @@ def main():
         args.iters = args.iters or 2000
         return run_denoise(args)
     return run_fit(args)
+
+
+def serving_leg(rimgs, n_fit, iters, mm_models=4, rate=50.0):
+    """Continuous batching against one request at a time on a short Poisson
+    stream: n_fit fit requests on the batched leg's ragged images (half of
+    them denoising, N(0, 0.05) added, as MM-RSMoE with mm_models models) and
+    as many render requests at 1-4x; the server admits by a 150 GB budget and
+    16 Mpx in flight (paper_2510_05814_gb300.serve)."""
+    import numpy as np
+    from paper_2510_05814_gb300 import serve
+    reqs = serve.poisson_workload(n_fit, n_fit, rate, iters=iters, mm_models=mm_models,
+                                  images=[t for t, _ in rimgs[:n_fit]])
+    srv = serve.Server(150 * (1 << 30), chunk=25, max_pixels=int(16e6))
+    t0 = time.perf_counter()
+    res_b = srv.run(reqs, realtime=True)
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res_p = serve.serve_plain(reqs, realtime=True)
+    t_p = time.perf_counter() - t0
+    byid = lambda rs: {r.rid: r for r in rs}
+    rb, rp = byid(res_b), byid(res_p)
+    fits = [r.rid for r in reqs if isinstance(r, serve.FitRequest)]
+    sb, sp = serve.latency_stats(res_b), serve.latency_stats(res_p)
+    return {"requests": len(reqs), "fits": len(fits), "iters": iters, "rate_per_s": rate,
+            "mm_models_per_denoising_request": mm_models,
+            "batched": {"wall_s": t_b, "req_per_s": len(reqs) / t_b, **sb},
+            "plain": {"wall_s": t_p, "req_per_s": len(reqs) / t_p, **sp},
+            "throughput_ratio": t_p / t_b, "p99_latency_ratio": sp["p99_s"] / sb["p99_s"],
+            "max_abs_psnr_diff_db": float(max(abs(rb[i].psnr - rp[i].psnr) for i in fits)),
+            "psnr_mean_db": float(np.mean([rb[i].psnr for i in fits])),
+            "how": "Poisson arrivals; the fit requests use the batched leg's first images; "
+                   "latency = result on the host - arrival; continuous batching vs one "
+                   "request at a time, one image per launch"}
 
 
 def roofline_fields(inrange, listed, tile_s, rates, sms, fallback_mhz, ncu):
@@ -958,8 +998,11 @@ def run_fit(args):
     fit_leg = batched = None
     if rank == 0 and world == 1 and args.fit_iters:
         fit_leg = fit_to_psnr_leg(wl, params0, args.fit_iters, args.fit_target_db)
+    serving = None
     if rank == 0 and world == 1 and rsizes:
         batched = batched_leg(rsizes, rimgs, args.batched_iters)
+        if args.serve_fits:
+            serving = serving_leg(rimgs, args.serve_fits, args.serve_iters)
 
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(local)
@@ -1024,6 +1067,7 @@ def run_fit(args):
                 "fit_iters": fit_leg["iters"], "psnr_final_db": fit_leg["psnr_final_db"]},
             "fit_to_psnr": fit_leg,
             "batched_vs_plain": batched,
+            "serving": serving,
             "sr_render_2x": {"ms": sr_ms, "pairs": sr_pairs, "out": f"{2 * W}x{2 * H}",
                              "Gpairs_per_s": sr_pairs / sr_ms / 1e6,
                              "model": "the initial kernels"},

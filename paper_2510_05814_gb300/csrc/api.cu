@@ -24,6 +24,7 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 struct Layout {
     size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
     size_t table, tile_off, pair_k, n_pairs, done, work, coef, part;
+    size_t kcnt, koff, kbsum, ktot, kn_long;
     size_t total;
 };
 
@@ -49,7 +50,14 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
         L.done = take(sizeof(uint32_t));
         L.work = take(sizeof(uint32_t));
         L.coef = take(sizeof(float) * 8 * (size_t)B);
-        L.part = det ? take(sizeof(float) * (size_t)GS * (size_t)pair_cap) : 0;
+        if (det) {
+            L.part = take(sizeof(float) * (size_t)GS * (size_t)pair_cap);
+            L.kcnt = take(sizeof(int32_t) * (size_t)K);
+            L.koff = take(sizeof(int32_t) * (size_t)(K + 1));
+            L.kbsum = take(sizeof(long long) * (size_t)scan_blocks_of(K));
+            L.ktot = take(sizeof(int64_t));
+            L.kn_long = take(sizeof(int32_t));
+        }
     }
     L.total = o;
     return L;
@@ -161,6 +169,8 @@ bool fit_geo(const smoe_fit_batch *bt, const smoe_fit_image *imgs, Geo *g,
         t_total += (int64_t)d.tiles_x * d.tiles_y;
     }
     if (K_total > 0x7fffffffLL || t_total > kMaxTiles) return false;
+    // the deterministic mode scans the kernels' pair counts (the prefix sum's capacity)
+    if (bt->deterministic && K_total > kMaxTiles) return false;
     Geo &G = *g;
     G = Geo{};
     G.C = bt->C;
@@ -301,7 +311,14 @@ static smoe_status fit_bufs(const smoe_fit_batch *batch, const smoe_fit_image *i
     w->pair_k = reinterpret_cast<int32_t *>(b + L->pair_k);
     w->n_pairs = reinterpret_cast<int64_t *>(b + L->n_pairs);
     w->work = reinterpret_cast<uint32_t *>(b + L->work);
-    w->part = batch->deterministic ? reinterpret_cast<float *>(b + L->part) : nullptr;
+    if (batch->deterministic) {
+        w->part = reinterpret_cast<float *>(b + L->part);
+        w->kcnt = reinterpret_cast<int32_t *>(b + L->kcnt);
+        w->koff = reinterpret_cast<int32_t *>(b + L->koff);
+        w->kbsum = reinterpret_cast<long long *>(b + L->kbsum);
+        w->ktot = reinterpret_cast<int64_t *>(b + L->ktot);
+        w->kn_long = reinterpret_cast<int32_t *>(b + L->kn_long);
+    }
     w->pair_cap = pair_cap;
     w->status = status;
     return SMOE_OK;

@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(kBinThreads, 4) k_prep_bbox(const __grid_const
         }
     }
     if (valid) w.rect[k] = rect;
+    if (valid && w.kcnt)    // deterministic fit: the kernel's pair count (rectangle area)
+        w.kcnt[k] = rect.x <= rect.z ? (rect.z - rect.x + 1) * (rect.w - rect.y + 1) : 0;
     walk_warp<false>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
 }
 
@@ -782,6 +784,13 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     if (g.K_total > 0) {
         const unsigned gb = (unsigned)((g.K_total + kBinThreads - 1) / kBinThreads);
         k_scatter<<<gb, kBinThreads, 0, st>>>(g, w);
+    }
+    if (w.kcnt && g.K_total > 0) {
+        // deterministic fit: each kernel's first slot (the same total as the
+        // tiles'; the offsets are written twice over, as offsets and cursors)
+        e = launch_exscan(g.K_total, w.kcnt, w.kbsum, w.koff, w.ktot, w.kn_long, w.koff,
+                          w.pair_cap, w.status, st);
+        if (e != cudaSuccess) return e;
     }
     return launch_sort_lists(g, w, st);
 }

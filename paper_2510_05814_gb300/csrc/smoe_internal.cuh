@@ -90,33 +90,43 @@ struct Bufs {
     int64_t pair_cap;
     int32_t *status;
     uint32_t *work;      // tile queue of the persistent fit launch (fit only)
-    float *part;         // deterministic fit: GS partial sums per (tile, kernel) pair, or null
+    // Deterministic fit (all null otherwise): GS partial sums per (tile,
+    // kernel) pair, kernel-major: kernel k's pairs occupy the koff[k] ..
+    // koff[k] + kcnt[k] - 1 slots, one per tile of its rectangle in row-major
+    // order (every tile of the rectangle lists the kernel); kcnt / koff are
+    // written by the binning (areas, then their exclusive scan).
+    float *part;
+    int32_t *kcnt, *koff;
+    long long *kbsum;    // scan block sums of the kernel areas
+    int64_t *ktot;       // their total (the pair count again)
+    int32_t *kn_long;    // unused output of the scan
 };
 
-// Deterministic gradient sums of kernel k: the partial sums of the (tile, k)
-// pairs added in row-major tile order (the pair's position in a tile's
-// ascending list is found by binary search).  GS sums, in registers.
+// Slot of the (tile (tx, ty) of its image, kernel k) pair in the
+// deterministic partial-sum buffer: the tile's row-major index inside the
+// kernel's rectangle rc, after the kernel's first slot.
+__device__ __forceinline__ int64_t part_slot(const Bufs &w, int64_t k, int4 rc, int tx, int ty) {
+    return (int64_t)w.koff[k] + (int64_t)(ty - rc.y) * (rc.z - rc.x + 1) + (tx - rc.x);
+}
+
+// Deterministic gradient sums of kernel k: the partial sums of its (tile, k)
+// pairs added in row-major tile order over its rectangle rc, which is the
+// order of its slots.  GS sums, in registers.
 template <int GS>
 __device__ __forceinline__ void gather_sums(const Bufs &w, const ImgDev &im, int64_t k, int4 rc,
                                             float (&out)[GS]) {
 #pragma unroll
     for (int q = 0; q < GS; ++q) out[q] = 0.0f;
-    for (int ty = rc.y; ty <= rc.w; ++ty)
-        for (int tx = rc.x; tx <= rc.z; ++tx) {
-            const int64_t t = im.t_off + (int64_t)ty * im.tiles_x + tx;
-            int lo = w.tile_off[t], hi = w.tile_off[t + 1];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (w.pair_k[mid] < k) lo = mid + 1; else hi = mid;
-            }
-            if (lo >= w.tile_off[t + 1] || w.pair_k[lo] != k) continue;
-            const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)lo * GS);
+    const int n = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
+    const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)w.koff[k] * GS);
+#pragma unroll 4
+    for (int i = 0; i < n; ++i) {
 #pragma unroll
-            for (int q = 0; q < GS / 4; ++q) {
-                const float4 v = src[q];
-                out[4 * q] += v.x; out[4 * q + 1] += v.y; out[4 * q + 2] += v.z; out[4 * q + 3] += v.w;
-            }
+        for (int q = 0; q < GS / 4; ++q) {
+            const float4 v = src[(int64_t)i * (GS / 4) + q];
+            out[4 * q] += v.x; out[4 * q + 1] += v.y; out[4 * q + 2] += v.z; out[4 * q + 3] += v.w;
         }
+    }
 }
 
 __host__ __device__ inline int rec_stride(int C, int linear) {

@@ -231,46 +231,60 @@ class FitBatch:
     def status_code(self):
         return smoe_get_status(self.status)
 
+    def _launch_iters(self, n, graph_iters):
+        """Enqueue n iterations: replays of the graph of graph_iters
+        iterations (captured on first use), the rest launched directly."""
+        if not graph_iters:
+            self.launch(n)
+            return
+        if self.graph is None or self.graph_iters != graph_iters:
+            self.capture(graph_iters)
+        reps = n // graph_iters
+        for _ in range(reps):
+            self.graph.replay()
+        if n - reps * graph_iters:
+            self.launch(n - reps * graph_iters)
+
     def run(self, n_iters, graph_iters=None, check_every=None):
         """Run n_iters iterations; with graph_iters, as replays of a captured
-        graph of that many iterations.  The status is checked after every
-        `check_every` iterations (default: at the end); a pair-buffer overflow
-        grows the buffer and resumes from where the run stopped."""
+        graph of that many iterations.  The status is checked (one host
+        synchronisation) after every `check_every` iterations (default: at
+        the end); the spatial re-sort runs every reorder_every iterations in
+        between, without a synchronisation.  A pair-buffer overflow stops the
+        batch at that iteration's binning (every later kernel, the re-sort
+        included, sees the status and does nothing): the buffer grows and the
+        run resumes from the iteration that overflowed."""
         done = 0
         check_every = check_every or n_iters
         while done < n_iters:
             chunk = min(check_every, n_iters - done)
-            if self.reorder_every:
-                chunk = min(chunk, self.reorder_every - self._since_reorder)
             before = self.step.clone()
-            if graph_iters:
-                if self.graph is None or self.graph_iters != graph_iters:
-                    self.capture(graph_iters)
-                reps = chunk // graph_iters
-                for _ in range(reps):
-                    self.graph.replay()
-                rest = chunk - reps * graph_iters
-                if rest:
-                    self.launch(rest)
-            else:
-                self.launch(chunk)
+            since0 = self._since_reorder
+            left = chunk
+            while left > 0:
+                seg = left
+                if self.reorder_every:
+                    seg = min(seg, self.reorder_every - self._since_reorder)
+                self._launch_iters(seg, graph_iters)
+                left -= seg
+                if self.reorder_every:
+                    self._since_reorder += seg
+                    if self._since_reorder >= self.reorder_every:
+                        self.reorder()
             st = self.status_code()
             if st == _lib.SMOE_ERR_CAPACITY:
                 # Grow the pair buffer and continue where the run stopped.
+                progressed = int((self.step - before).max().item())
                 self.pair_cap = int(self.pair_cap * 1.5) + 4096
                 self._setup(reset=False)
-                progressed = int((self.step - before).max().item())
                 done += progressed
                 if self.reorder_every:
-                    self._since_reorder += progressed
+                    # the re-sorts up to the overflow ran, the later ones did nothing
+                    self._since_reorder = (since0 + progressed) % self.reorder_every
                 continue
             if st != _lib.SMOE_OK:
                 raise SmoeError(st, "smoe_fit")
             done += chunk
-            if self.reorder_every:
-                self._since_reorder += chunk
-                if self._since_reorder >= self.reorder_every:
-                    self.reorder()
         return self
 
     def render_mean(self, out=None, stream=None):

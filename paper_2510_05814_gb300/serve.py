@@ -371,12 +371,13 @@ def latency_stats(results):
 
 
 def poisson_workload(n_fit, n_render, rate, seed=5, iters=500, sizes=None, noise_var=0.05,
-                     render_scales=(1.0, 4.0), mm_models=1):
+                     render_scales=(1.0, 4.0), mm_models=1, images=None):
     """Fit requests with sizes from `sizes` (default: the ragged size
     distribution, 128x96 .. 1920x1080), half of them denoising requests with
     N(0, noise_var) added (MM-RSMoE with `mm_models` models when > 1);
     render requests on earlier fits at scales drawn from U[render_scales];
-    Poisson arrivals at `rate` per second."""
+    Poisson arrivals at `rate` per second.  `images`: (C, H, W) images to use
+    for the fit requests in turn instead of drawing new ones."""
     rng = np.random.default_rng(seed)
     sizes = sizes or synth.ragged_sizes(n_fit, seed)
     n = n_fit + n_render
@@ -389,9 +390,12 @@ def poisson_workload(n_fit, n_render, rate, seed=5, iters=500, sizes=None, noise
     reqs, fit_ids, fi = [], [], 0
     for i, (a, k) in enumerate(zip(arrivals, kinds)):
         if k == "fit" or not fit_ids:
-            W, H = sizes[fi % len(sizes)]
+            if images is not None:
+                img = np.array(images[fi % len(images)], np.float32)
+            else:
+                W, H = sizes[fi % len(sizes)]
+                img = synth.polygon_image(W, H, 3, 12, seed * 1000 + i, texture_amp=0.1)
             fi += 1
-            img = synth.polygon_image(W, H, 3, 12, seed * 1000 + i, texture_amp=0.1)
             den = (len(fit_ids) % 2) == 1
             if den:
                 img = (img + rng.normal(0.0, np.sqrt(noise_var), img.shape)).astype(np.float32)

@@ -109,3 +109,33 @@ def test_reorder_then_render_matches_oracle():
                              with_scale=True)
     err = np.abs(y.cpu().numpy() - ref)
     assert np.all(err <= 1e-5 * np.maximum(np.abs(ref), absm))
+
+
+def test_run_with_overflow_keeps_the_resort_schedule():
+    """FitBatch.run checks the status only at the end here, re-sorting every
+    4 iterations in between; a pair buffer that overflows (at once, or when
+    the lists outgrow the initial count) stops the batch at that
+    iteration's binning, grows, and resumes with the re-sort at the same
+    iterations: the deterministic fit equals the one with room to spare,
+    bit for bit."""
+    t = synth.polygon_image(64, 48, 3, 5, 910, texture_amp=0.1)
+    p = synth.init_params(t, 192, 3.0, True, 910, aniso=(1.0, 2.0), slope_std=0.02)
+    tt = torch.tensor(t, device="cuda")
+    lr = (4e-4, 4e-4, 1e-2, 1e-2, 1e-2)
+    desc = api.RasterDesc(64, 48, 3, 8, True)
+    n0 = int(api.Rasterizer(desc, p.K).bin(api.SMoEParams.from_numpy(p)).n_pairs.item())
+
+    def fit(cap):
+        fb = FitBatch([tt], [api.SMoEParams.from_numpy(p)], 12, lr=lr, tile=8, reorder_every=4,
+                      deterministic=True, pair_cap=cap)
+        return fb.run(12, graph_iters=2)
+
+    ref = fit(4 * n0)
+    for cap in (64, n0):
+        got = fit(cap)
+        assert int(got.step.item()) == 12
+        # the reported MSE adds per-tile FP64 partial sums in completion order
+        np.testing.assert_allclose(got.losses(), ref.losses(), rtol=1e-12)
+        for a, b in zip(got.params_of(0).tensors(), ref.params_of(0).tensors()):
+            assert torch.equal(a, b)
+    assert fit(64).pair_cap > 64
