@@ -24,7 +24,7 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 struct Layout {
     size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
     size_t table, tile_off, pair_k, n_pairs, done, work, coef, part;
-    size_t kcnt, koff, kbsum, ktot, kn_long;
+    size_t kcnt, koff, kbsum, ktot, kn_long, pidx;
     size_t total;
 };
 
@@ -57,6 +57,7 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
             L.kbsum = take(sizeof(long long) * (size_t)scan_blocks_of(K));
             L.ktot = take(sizeof(int64_t));
             L.kn_long = take(sizeof(int32_t));
+            L.pidx = take(sizeof(int32_t) * (size_t)pair_cap);
         }
     }
     L.total = o;
@@ -318,6 +319,7 @@ static smoe_status fit_bufs(const smoe_fit_batch *batch, const smoe_fit_image *i
         w->kbsum = reinterpret_cast<long long *>(b + L->kbsum);
         w->ktot = reinterpret_cast<int64_t *>(b + L->ktot);
         w->kn_long = reinterpret_cast<int32_t *>(b + L->kn_long);
+        w->pidx = reinterpret_cast<int32_t *>(b + L->pidx);
     }
     w->pair_cap = pair_cap;
     w->status = status;

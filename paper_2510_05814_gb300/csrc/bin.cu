@@ -767,6 +767,23 @@ __device__ void segsort_tile(const Geo &g, const Bufs &w, int64_t t, uint32_t *s
 
 }  // namespace
 
+// Deterministic fit: the kernel-major index of the pairs' list positions
+// (see Bufs::pidx).  One warp per tile, lanes over its list.
+__global__ void __launch_bounds__(kShortSortThreads) k_pair_index(const __grid_constant__ Geo g,
+                                                                  Bufs w) {
+    if (status_bad(w.status)) return;
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= g.tiles_total) return;
+    const ImgDev &im = img_of(g, img_by_tile(g, t));
+    const int64_t local = t - im.t_off;
+    const int tx = (int)(local % im.tiles_x), ty = (int)(local / im.tiles_x);
+    const int32_t p0 = w.tile_off[t], p1 = w.tile_off[t + 1];
+    for (int32_t p = p0 + (int32_t)(threadIdx.x & 31); p < p1; p += 32) {
+        const int32_t k = w.pair_k[p];
+        w.pidx[part_slot(w, k, w.rect[k], tx, ty)] = p;
+    }
+}
+
 cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     const int64_t n = g.tiles_total;
     cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * n, st);
@@ -786,13 +803,20 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
         k_scatter<<<gb, kBinThreads, 0, st>>>(g, w);
     }
     if (w.kcnt && g.K_total > 0) {
-        // deterministic fit: each kernel's first slot (the same total as the
-        // tiles'; the offsets are written twice over, as offsets and cursors)
+        // deterministic fit: each kernel's first index entry (the same total
+        // as the tiles'; the offsets are written twice over, as offsets and
+        // cursors)
         e = launch_exscan(g.K_total, w.kcnt, w.kbsum, w.koff, w.ktot, w.kn_long, w.koff,
                           w.pair_cap, w.status, st);
         if (e != cudaSuccess) return e;
     }
-    return launch_sort_lists(g, w, st);
+    e = launch_sort_lists(g, w, st);
+    if (e == cudaSuccess && w.kcnt && n > 0) {
+        constexpr int wpb = kShortSortThreads / 32;
+        k_pair_index<<<(unsigned)((n + wpb - 1) / wpb), kShortSortThreads, 0, st>>>(g, w);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 cudaError_t launch_sort_lists(const Geo &g, const Bufs &w, cudaStream_t st) {

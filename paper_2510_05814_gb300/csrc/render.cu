@@ -686,9 +686,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             const uint32_t rowsel = every << base;
             if (sub == 0 && (m & rowsel)) {
                 if (w.part) {        // deterministic: this pair's own slot
-                    const int kid = sm.kid[j];
-                    float4 *dst = reinterpret_cast<float4 *>(
-                        w.part + part_slot(w, kid, w.rect[kid], ti.x0 / T, ti.y0 / T) * R::GS);
+                    float4 *dst = reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS);
 #pragma unroll
                     for (int q = 0; q < R::GS / 4; ++q)
                         dst[q] = make_float4(acc.v[4 * q], acc.v[4 * q + 1], acc.v[4 * q + 2],
@@ -714,9 +712,8 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             for (int i = threadIdx.x; i < nc * (R::GS / 4); i += kThreads) {
                 const int j = i / (R::GS / 4), q = i - j * (R::GS / 4);
                 if (!sm.mask[j])
-                    reinterpret_cast<float4 *>(
-                        w.part + part_slot(w, sm.kid[j], w.rect[sm.kid[j]], ti.x0 / T, ti.y0 / T) *
-                                     R::GS)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    reinterpret_cast<float4 *>(w.part + (ti.start + c0 + j) * R::GS)[q] =
+                        make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
     }

@@ -91,39 +91,42 @@ struct Bufs {
     int32_t *status;
     uint32_t *work;      // tile queue of the persistent fit launch (fit only)
     // Deterministic fit (all null otherwise): GS partial sums per (tile,
-    // kernel) pair, kernel-major: kernel k's pairs occupy the koff[k] ..
-    // koff[k] + kcnt[k] - 1 slots, one per tile of its rectangle in row-major
-    // order (every tile of the rectangle lists the kernel); kcnt / koff are
-    // written by the binning (areas, then their exclusive scan).
+    // kernel) pair at the pair's list position, and a kernel-major index of
+    // those positions: kernel k's pairs are pidx[koff[k] .. koff[k] +
+    // kcnt[k] - 1], one per tile of its rectangle in row-major order (every
+    // tile of the rectangle lists the kernel).  kcnt / koff / pidx are
+    // written by the binning (areas, their exclusive scan, the index).
     float *part;
-    int32_t *kcnt, *koff;
+    int32_t *kcnt, *koff, *pidx;
     long long *kbsum;    // scan block sums of the kernel areas
     int64_t *ktot;       // their total (the pair count again)
     int32_t *kn_long;    // unused output of the scan
 };
 
-// Slot of the (tile (tx, ty) of its image, kernel k) pair in the
-// deterministic partial-sum buffer: the tile's row-major index inside the
-// kernel's rectangle rc, after the kernel's first slot.
+// Index entry of the (tile (tx, ty) of its image, kernel k) pair: the
+// tile's row-major position inside the kernel's rectangle rc, after the
+// kernel's first entry.
 __device__ __forceinline__ int64_t part_slot(const Bufs &w, int64_t k, int4 rc, int tx, int ty) {
     return (int64_t)w.koff[k] + (int64_t)(ty - rc.y) * (rc.z - rc.x + 1) + (tx - rc.x);
 }
 
 // Deterministic gradient sums of kernel k: the partial sums of its (tile, k)
-// pairs added in row-major tile order over its rectangle rc, which is the
-// order of its slots.  GS sums, in registers.
+// pairs added in row-major tile order over its rectangle rc (the order of
+// its index entries).  The loads are independent of each other.  GS sums,
+// in registers.
 template <int GS>
 __device__ __forceinline__ void gather_sums(const Bufs &w, const ImgDev &im, int64_t k, int4 rc,
                                             float (&out)[GS]) {
 #pragma unroll
     for (int q = 0; q < GS; ++q) out[q] = 0.0f;
     const int n = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-    const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)w.koff[k] * GS);
+    const int32_t *idx = w.pidx + w.koff[k];
 #pragma unroll 4
     for (int i = 0; i < n; ++i) {
+        const float4 *src = reinterpret_cast<const float4 *>(w.part + (int64_t)idx[i] * GS);
 #pragma unroll
         for (int q = 0; q < GS / 4; ++q) {
-            const float4 v = src[(int64_t)i * (GS / 4) + q];
+            const float4 v = src[q];
             out[4 * q] += v.x; out[4 * q + 1] += v.y; out[4 * q + 2] += v.z; out[4 * q + 3] += v.w;
         }
     }
