@@ -173,3 +173,23 @@ def test_fit_gradients_argument_errors():
                                 api._ptr(fb.ws), fb.ws.numel(), ctypes.byref(bad.c()),
                                 api._ptr(fb.status), api._stream(None))
     assert st == _lib.SMOE_ERR_ARG
+
+
+@pytest.mark.parametrize("C,linear,tile", [(3, True, 8), (1, False, 16)])
+def test_fit_gradients_degenerate_kernels(C, linear, tile):
+    """Degenerate kernels (a NaN centre, an infinite or a zero Cholesky
+    entry, centres off the raster, a kernel far narrower than a pixel): the
+    fused path's read-out matches the oracle's gradient, and a kernel listed
+    in no tile gets exactly 0."""
+    from test_gpu_parity import degenerate_case
+    W, H = 41, 39
+    p = degenerate_case(W, H, C, linear)
+    t = synth.polygon_image(W, H, C, 4, 350 + C, texture_amp=0.1)
+    fb = FitBatch([torch.tensor(t, device="cuda")], [api.SMoEParams.from_numpy(p)], 2, lr=LR,
+                  tile=tile)
+    g = fb.gradients()[0]
+    assert fb.status_code() == 0
+    ref, terms = oracle_grads(p, t, tile)
+    compare(g, ref, terms, f"degenerate C={C}")
+    nan_k = 9                                  # mu = (nan, 0.5): listed in no tile
+    assert all(float(x[nan_k].abs().sum()) == 0.0 for x in g.tensors())
