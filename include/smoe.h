@@ -196,10 +196,13 @@ typedef struct {
     int32_t persistent;     /* 1: the fused tile kernel runs as one persistent grid that
                                takes tiles from a work queue; 0: one CTA per tile */
     int32_t deterministic;  /* 1: every (tile, kernel) pair writes its partial gradient
-                               sums to its own slot and the Adam step adds them in a fixed
-                               tile order, so a fit is bit-reproducible and independent of
-                               the other images in the batch (costs 64 B per pair of
-                               workspace); 0: float atomics (faster, order-dependent) */
+                               sums to its own slot and the Adam step adds a kernel's
+                               slots in row-major tile order (through an index of them
+                               the binning builds), so a fit is bit-reproducible and
+                               independent of the other images in the batch (costs 68 B
+                               per pair and 8 B per kernel of workspace; at most
+                               16.7 M kernels in the batch); 0: float atomics (faster,
+                               order-dependent) */
     int32_t gate;           /* as smoe_desc.gate: 0 softmax gates, 1 RBF sum */
 } smoe_fit_batch;
 
