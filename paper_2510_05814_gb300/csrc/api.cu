@@ -22,7 +22,7 @@ int64_t scan_blocks_of(int64_t n) { return (n + 4095) / 4096; }
 
 // Workspace regions, in order; `fit` adds the batch table and the lists.
 struct Layout {
-    size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc;
+    size_t rec, rect, tile_cnt, cursor, bsum, long_q, n_long, pair_tmp, acc, huge, n_huge;
     size_t table, tile_off, pair_k, n_pairs, done, work, coef, part;
     size_t kcnt, koff, kbsum, ktot, kn_long, pidx;
     size_t total;
@@ -42,6 +42,8 @@ Layout layout(int64_t K, int64_t tiles, int64_t pair_cap, int S, int GS, int B, 
     L.long_q = take(sizeof(int32_t) * (size_t)tiles);
     L.n_long = take(sizeof(int32_t));
     L.acc = take(sizeof(float) * (size_t)GS * (size_t)K);
+    L.huge = take(sizeof(int32_t) * (size_t)K);
+    L.n_huge = take(sizeof(int32_t));
     L.pair_tmp = take(sizeof(int32_t) * (size_t)pair_cap);
     if (fit) {
         L.tile_off = take(sizeof(int32_t) * (size_t)(tiles + 1));
@@ -112,6 +114,8 @@ Bufs make_bufs(void *ws, const Layout &L) {
     w.long_q = reinterpret_cast<int32_t *>(b + L.long_q);
     w.n_long = reinterpret_cast<int32_t *>(b + L.n_long);
     w.acc = reinterpret_cast<float *>(b + L.acc);
+    w.huge = reinterpret_cast<int32_t *>(b + L.huge);
+    w.n_huge = reinterpret_cast<int32_t *>(b + L.n_huge);
     return w;
 }
 

@@ -32,7 +32,13 @@ constexpr int kSortThreads = 256;
 constexpr int kSortMax = 2048;                 // bitonic in shared memory up to this
 constexpr int kBitmapWords = 8192;             // 262144 kernel ids per bitmap pass
 constexpr int kLongGrid = 152;                 // CTAs sweeping the queue of long lists (> 512 ids)
-constexpr int kBig = 32;                       // rectangles of more tiles are walked by a whole warp
+#ifndef SMOE_BIN_BIG
+#define SMOE_BIN_BIG 32
+#endif
+#ifndef SMOE_BIN_AGG
+#define SMOE_BIN_AGG 128
+#endif
+constexpr int kBig = SMOE_BIN_BIG;             // rectangles of more tiles are walked by a whole warp
 // The scatter marks the first id of every block it writes contiguously and
 // in ascending order (a warp's covering kernels, or a single id) in the top
 // bit of the 32-bit slot; ids are below 2^31.  The sorts strip it.
@@ -122,7 +128,7 @@ __device__ __forceinline__ void walk_rects(const Bufs &w, bool valid, int4 rect,
 // two images, holds more than kAggMax tiles or no fewer tiles than the small
 // rectangles' total walk lane by lane (walk_rects).  Both passes take the
 // same decisions from the same rectangles, so counts and slots agree.
-constexpr int kAggMax = 128;
+constexpr int kAggMax = SMOE_BIN_AGG;
 constexpr int kBinThreads = 256;
 
 struct WarpAgg {
@@ -226,6 +232,11 @@ __device__ __forceinline__ void walk_warp(const Bufs &w, bool valid, int4 rect, 
         }
     }
     __syncwarp();
+}
+
+// A rectangle the binning queues instead of walking (see Bufs::huge).
+__device__ __forceinline__ bool is_huge(const Bufs &w, int4 r) {
+    return w.huge && r.x <= r.z && (r.z - r.x + 1) * (r.w - r.y + 1) > kHugeRect;
 }
 
 __global__ void __launch_bounds__(kBinThreads, 4) k_prep_bbox(const __grid_constant__ Geo g, Bufs w) {
@@ -335,7 +346,12 @@ __global__ void __launch_bounds__(kBinThreads, 4) k_prep_bbox(const __grid_const
     if (valid) w.rect[k] = rect;
     if (valid && w.kcnt)    // deterministic fit: the kernel's pair count (rectangle area)
         w.kcnt[k] = rect.x <= rect.z ? (rect.z - rect.x + 1) * (rect.w - rect.y + 1) : 0;
-    walk_warp<false>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
+    int4 walk = rect;
+    if (valid && is_huge(w, rect)) {      // counted per tile by k_huge_cover instead
+        w.huge[atomicAdd(w.n_huge, 1)] = (int32_t)k;
+        walk = make_int4(0, 0, -1, -1);
+    }
+    walk_warp<false>(w, valid, walk, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
 }
 
 // Block-wide exclusive scan of one long long per thread (1024 threads).
@@ -441,9 +457,51 @@ __global__ void __launch_bounds__(kBinThreads) k_scatter(const __grid_constant__
     const int64_t k_raw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool valid = k_raw < g.K_total;
     const int64_t k = valid ? k_raw : g.K_total - 1;
-    const int4 rect = w.rect[k];
+    int4 rect = w.rect[k];
+    if (is_huge(w, rect)) rect = make_int4(0, 0, -1, -1);   // appended by k_segsort_warp
     const ImgDev &im = img_of(g, img_by_kernel(g, k));
     walk_warp<true>(w, valid, rect, im.t_off, im.tiles_x, (int32_t)k, agg[threadIdx.x >> 5]);
+}
+
+// Coverage of the queued (huge) rectangles, one thread per tile: each tile's
+// count gains the number of queued rectangles of its image that hold it (the
+// count kernel's atomics are complete; the prefix sum follows).
+constexpr int kHugeThreads = 256;
+
+__global__ void __launch_bounds__(kHugeThreads) k_huge_cover(const __grid_constant__ Geo g,
+                                                             Bufs w) {
+    __shared__ int4 hr[kHugeThreads];
+    __shared__ int hb[kHugeThreads];
+    if (status_bad(w.status)) return;
+    const int nh = *w.n_huge;
+    if (nh == 0) return;                      // the same for every thread
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool in = t < g.tiles_total;
+    int b = -1, tx = 0, ty = 0;
+    if (in) {
+        b = img_by_tile(g, t);
+        const ImgDev &im = img_of(g, b);
+        const int64_t local = t - im.t_off;
+        tx = (int)(local % im.tiles_x);
+        ty = (int)(local / im.tiles_x);
+    }
+    int cnt = 0;
+    for (int c0 = 0; c0 < nh; c0 += kHugeThreads) {
+        __syncthreads();
+        const int i = c0 + (int)threadIdx.x;
+        if (i < nh) {
+            const int32_t k = w.huge[i];
+            hr[threadIdx.x] = w.rect[k];
+            hb[threadIdx.x] = img_by_kernel(g, k);
+        }
+        __syncthreads();
+        const int m = min(kHugeThreads, nh - c0);
+        for (int j = 0; j < m; ++j) {
+            const int4 r = hr[j];
+            cnt += (hb[j] == b && r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w) ? 1 : 0;
+        }
+    }
+    if (in && cnt) w.tile_cnt[t] += cnt;
 }
 
 __device__ int block_exscan_int(int v, int *total) {
@@ -646,12 +704,40 @@ __device__ __forceinline__ bool warp_merge_runs(const Bufs &w, int64_t start, in
 // queued for k_segsort_long.
 constexpr int kShortSortThreads = 128;
 
-__global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(int64_t n_tiles, Bufs w) {
+__global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(const __grid_constant__ Geo g,
+                                                                    int64_t n_tiles, Bufs w) {
     __shared__ WarpRuns runs[kShortSortThreads / 32];
     if (status_bad(w.status)) return;
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= n_tiles) return;
+    if (w.huge) {
+        // the queued (huge) kernels that hold this tile go after the slots the
+        // scatter filled, up to the tile's end, each as its own block
+        const int nh = *w.n_huge;
+        if (nh > 0) {
+            const int b = img_by_tile(g, t);
+            const ImgDev &im = img_of(g, b);
+            const int64_t local = t - im.t_off;
+            const int tx = (int)(local % im.tiles_x), ty = (int)(local / im.tiles_x);
+            int32_t at = w.cursor[t];
+            for (int i0 = 0; i0 < nh; i0 += 32) {
+                const int i = i0 + lane;
+                int32_t k = 0;
+                bool cov = false;
+                if (i < nh) {
+                    k = w.huge[i];
+                    const int4 r = w.rect[k];
+                    cov = img_by_kernel(g, k) == b && r.x <= tx && tx <= r.z && r.y <= ty &&
+                          ty <= r.w;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                if (cov) w.pair_tmp[at + __popc(bal & ((1u << lane) - 1u))] = k | kBlockHead;
+                at += __popc(bal);
+            }
+            __syncwarp();
+        }
+    }
     const int64_t start = w.tile_off[t];
     const int n = (int)(w.tile_off[t + 1] - start);
     if (n <= 1) {
@@ -787,10 +873,14 @@ __global__ void __launch_bounds__(kShortSortThreads) k_pair_index(const __grid_c
 cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
     const int64_t n = g.tiles_total;
     cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * n, st);
+    if (e == cudaSuccess && w.huge) e = cudaMemsetAsync(w.n_huge, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     if (g.K_total > 0) {
         const unsigned gb = (unsigned)((g.K_total + kBinThreads - 1) / kBinThreads);
         k_prep_bbox<<<gb, kBinThreads, 0, st>>>(g, w);
+        if (w.huge && n > 0)
+            k_huge_cover<<<(unsigned)((n + kHugeThreads - 1) / kHugeThreads), kHugeThreads, 0, st>>>(
+                g, w);
     }
     const int nb = (int)((n + kScanChunk - 1) / kScanChunk);
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(n, w.tile_cnt, w.bsum, w.status);
@@ -823,7 +913,7 @@ cudaError_t launch_sort_lists(const Geo &g, const Bufs &w, cudaStream_t st) {
     const int64_t n = g.tiles_total;
     if (n > 0) {
         constexpr int wpb = kShortSortThreads / 32;
-        k_segsort_warp<<<(unsigned)((n + wpb - 1) / wpb), kShortSortThreads, 0, st>>>(n, w);
+        k_segsort_warp<<<(unsigned)((n + wpb - 1) / wpb), kShortSortThreads, 0, st>>>(g, n, w);
         const int64_t gl = n < kLongGrid ? n : kLongGrid;
         k_segsort_long<<<(unsigned)gl, kSortThreads, 0, st>>>(g, w);
     }

@@ -20,12 +20,15 @@
 // shared memory.
 //
 // Backward (row-synchronous, lane = kernel): the chunk's kernels are grouped
-// 32 at a time by the centre of their row span; a warp walks the union of its
-// group's row masks, every lane evaluating its own kernel on the row's pixel
-// pairs against the pixel state read by broadcast from shared memory, and
-// keeps its kernel's raw sums (below) in registers until one float4 atomic
-// per 4 sums per (tile, kernel).  With float atomics the last round's groups
-// are shared by all warps row-interleaved, so no warp idles.
+// 16 at a time by the centre of their row span; a warp walks the rows where
+// its group has a live row two at a time, lanes 0-15 on the first and 16-31
+// on the second, every lane evaluating its kernel on the row's pixel pairs
+// against the pixel state read by broadcast from shared memory; a kernel's
+// raw sums (below) stay in its two lanes' registers, are added once, and
+// leave the SM as one float4 atomic per 4 sums per (tile, kernel).  With
+// float atomics the last round's groups are shared by all warps
+// row-interleaved, so no warp idles.  The chunks of a long list are walked
+// last to first (the forward's last chunk is still staged).
 //
 // Raw per-kernel sums (e = pi exp(-q/2); s = g sum_c G_c (m_c - y_c), g = e / D,
 // H_c = G_c / D, so s = e (sum_c H_c m_c - sum_c H_c y_c) and g G_c = e H_c;
@@ -494,14 +497,12 @@ struct BwdAcc {
 };
 
 // Backward over the tile's list; the pixel state is in sm.pst.  `staged`:
-// the first chunk is still in shared memory from the forward.  Each lane
-// owns one kernel of the chunk (kernels with an empty row mask are dropped;
-// the rest are grouped by the centre of their row span so that a warp's 32
-// kernels cover similar rows) and the warp walks the union of its kernels'
-// rows together:
-// every read of pixel state is a broadcast, lanes whose kernel misses the
-// row contribute zero, and each kernel's sums stay in its lane's registers
-// until one float4 atomic per 4 sums at the end.
+// the forward's last chunk is still in shared memory.  The chunk's kernels
+// with a live row are grouped by the centre of their row span, 16 to a
+// warp; a lane owns one kernel and every second row of the group's rows
+// (see `group` below): every read of pixel state is a broadcast, lanes
+// whose kernel misses the row contribute zero, and each kernel's sums stay
+// in its two lanes' registers until one float4 atomic per 4 sums at the end.
 template <int C, bool LIN, int T>
 __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
                                          Smem<C, LIN, T> &sm, bool staged) {
@@ -511,10 +512,14 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
     const float2 k2 = f2(kNegHalfLog2e);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float x0f = (float)ti.x0, y0f = (float)ti.y0 + 0.5f;   // exact: integers < 2^24
-    for (int c0 = 0; c0 < ti.n; c0 += G::NCH) {
+    // The chunks last to first: the forward leaves its last chunk staged, so
+    // a list longer than one chunk is staged once less (each kernel's sums
+    // come from the one chunk that holds it, so the order changes none).
+    const int last = ti.n > 0 ? (ti.n - 1) / G::NCH * G::NCH : 0;
+    for (int c0 = last; c0 >= 0; c0 -= G::NCH) {
         const int nc = min(G::NCH, ti.n - c0);
         __syncthreads();                          // previous users of the chunk are done
-        if (!(staged && c0 == 0 && ti.n <= G::NCH)) stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
+        if (!(staged && c0 == last)) stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
         // Group the kernels by the centre of their row span, first + last row
         // (counting sort over 2T - 1 keys), so that a warp's 32 kernels cover
         // similar rows; kernels that miss every row are dropped.  The order

@@ -130,6 +130,7 @@ cudaError_t launch_reorder(const Geo &g, const Bufs &w, int32_t *order, cudaStre
     Bufs r = w;
     r.pair_tmp = tmp;
     r.pair_k = ids;
+    r.huge = nullptr;                  // the centre lists have no queued kernels
     cudaError_t e = cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * n, st);
     if (e != cudaSuccess) return e;
     k_centre_count<<<blocks_for(K), kThreads, 0, st>>>(g, r);

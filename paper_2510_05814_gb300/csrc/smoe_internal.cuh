@@ -27,6 +27,8 @@
 namespace smoe {
 
 constexpr int kMaxC = 3;
+// Rectangles of more tiles than this are queued by the binning (Bufs::huge).
+constexpr int kHugeRect = 1024;
 // Largest cutoff: exp(-q/2) of an included pair stays an FP32 normal number
 // (q log2(e) / 2 <= 125.5), so no included kernel is flushed to zero.
 constexpr float kMaxQmax = 174.0f;
@@ -90,6 +92,13 @@ struct Bufs {
     int64_t pair_cap;
     int32_t *status;
     uint32_t *work;      // tile queue of the persistent fit launch (fit only)
+    // Kernels whose rectangle holds more than kHugeRect tiles (a kernel that
+    // a near-zero Cholesky entry stretches across the image): the binning
+    // queues their ids here instead of walking their tiles, adds their
+    // coverage to the tile counts one thread per tile and appends them to
+    // each covered tile's list before the sort.  Null: every kernel walked.
+    int32_t *huge;
+    int32_t *n_huge;
     // Deterministic fit (all null otherwise): GS partial sums per (tile,
     // kernel) pair at the pair's list position, and a kernel-major index of
     // those positions: kernel k's pairs are pidx[koff[k] .. koff[k] +

@@ -19,6 +19,7 @@ if not torch.cuda.is_available():
 
 import oracle as om  # noqa: E402
 from paper_2510_05814_gb300 import api, synth  # noqa: E402
+from paper_2510_05814_gb300.fit import FitBatch  # noqa: E402
 
 RTOL_Y = 1e-5
 RTOL_G = 1e-4
@@ -185,3 +186,64 @@ def test_batch_warps_straddling_images_with_offimage_kernels():
         np.testing.assert_allclose(fb.losses()[b, :3], one.losses()[0, :3], rtol=1e-12)
         for x, y in zip(fb.params_of(b).tensors(), one.params_of(0).tensors()):
             assert torch.equal(x, y)
+
+
+def huge_case(W, H, seed, C=3):
+    """Normal kernels plus kernels whose box holds more than 1024 tiles at
+    T = 16: degenerate ones (a zero Cholesky entry: every tile), stripes (a
+    near-zero entry stretching the kernel across the raster) and a very wide
+    round one."""
+    rng = np.random.default_rng(seed)
+    K = 160
+    mu = rng.uniform(0.05, 0.95, (K, 2))
+    s = rng.uniform(2.0, 6.0, K)
+    chol = np.stack([1 / s, rng.normal(0, 0.05, K), 1 / s], 1)
+    chol[0] = (0.0, 0.3, 0.3)                    # det = 0: every tile
+    chol[1] = (0.3, 0.0, 0.0)                    # det = 0 (c = 0)
+    chol[2] = (1e-4, 0.0, 0.4)                   # a horizontal stripe
+    chol[3] = (0.5, 0.0, 2e-4)                   # a vertical stripe
+    chol[4] = (1e-3, 0.02, 1e-3)                 # very wide
+    ea = rng.uniform(0, 1, (K, C))
+    eW = rng.normal(0, 0.02, (K, C, 2))
+    return synth.Params(mu.astype(np.float32), chol.astype(np.float32), ea.astype(np.float32),
+                        eW.astype(np.float32))
+
+
+def test_huge_rectangles_are_binned_bit_exact():
+    """Rectangles of more than 1024 tiles are counted and appended per tile
+    instead of walked: the lists stay the oracle's, bit for bit, and the
+    render and backward stay within the bars."""
+    W, H = 1024, 768                                       # 64 x 48 = 3072 tiles
+    p = huge_case(W, H, 71)
+    m = om.Model(W, H, 3, p.mu, p.chol, p.ea, p.eW, tile=16)
+    rects = [om.rect(m, k)[1] for k in range(5)]
+    assert min(rects) > 1024
+    params = api.SMoEParams.from_numpy(p)
+    r = api.Rasterizer(api.RasterDesc(W, H, 3, 16, True), params.K).bin(params)
+    off, pk = r.lists()
+    ref_off, ref_pk = om.bin_tiles(m)
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
+    y, inv = r.render()
+    rng = np.random.default_rng(72)
+    px = rng.choice(W * H, 400, replace=False)
+    ref, _, absm = om.render(m, pixels=px, with_scale=True)
+    got = y.reshape(3, -1)[:, torch.tensor(px, device="cuda")].cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.maximum(np.abs(ref), absm))
+
+
+def test_huge_rectangles_in_a_batch_stay_in_their_image():
+    """A deterministic batch of two images, each with huge rectangles: every
+    image's fit equals its fit alone, bit for bit (a queued kernel is added
+    to its own image's tiles only)."""
+    ts, ps = [], []
+    for i, (W, H) in enumerate([(640, 512), (512, 640)]):
+        ts.append(torch.tensor(synth.polygon_image(W, H, 3, 5, 80 + i), device="cuda"))
+        ps.append(api.SMoEParams.from_numpy(huge_case(W, H, 90 + i)))
+    lr = (1e-4, 1e-4, 1e-3, 1e-2, 1e-2)
+    both = FitBatch(ts, [p.clone() for p in ps], 3, lr=lr, deterministic=True).run(3)
+    for b in range(2):
+        one = FitBatch([ts[b]], [ps[b].clone()], 3, lr=lr, deterministic=True).run(3)
+        for x, y in zip(both.params_of(b).tensors(), one.params_of(0).tensors()):
+            assert torch.equal(x, y)
+        np.testing.assert_allclose(both.losses()[b], one.losses()[0], rtol=1e-12)
