@@ -58,9 +58,9 @@ REORDER_KERNELS = 15
 # operations (FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) thread
 # instructions); valid only while render.cu's code (comments and whitespace
 # aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "5b9c1c57ba09f0706eaeebc3c0ea6da0e03c664e26e1d3e4697cc4eb4ac3700e",
-       "bytes_per_launch": 103.111424e6, "fma_pipe_active": 0.614, "issue_active": 0.627,
-       "xu_active": 0.137, "fp32_lane_ops": 14.632777877e9}
+NCU = {"render_cu_code_sha256": "4986d06fe36a3d2675b36b88993e9f6a87a1d50866d5a4e7e8c7de1c39a7236c",
+       "bytes_per_launch": 103.716864e6, "fma_pipe_active": 0.6145, "issue_active": 0.6268,
+       "xu_active": 0.1367, "fp32_lane_ops": 14.632718837e9}
 
 def issue_rates():
     """Measured lane operations per clock per SM of ex2 / FFMA / packed
