@@ -733,7 +733,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "batched":
-        args.iters = args.iters or 200
+        args.iters = args.iters or 1000
         return run_batched(args)
     if args.mode == "serve":
         args.iters = args.iters or 500
