@@ -28,7 +28,10 @@ namespace smoe {
 
 constexpr int kMaxC = 3;
 // Rectangles of more tiles than this are queued by the binning (Bufs::huge).
-constexpr int kHugeRect = 1024;
+#ifndef SMOE_HUGE_RECT
+#define SMOE_HUGE_RECT 1024
+#endif
+constexpr int kHugeRect = SMOE_HUGE_RECT;
 // Largest cutoff: exp(-q/2) of an included pair stays an FP32 normal number
 // (q log2(e) / 2 <= 125.5), so no included kernel is flushed to zero.
 constexpr float kMaxQmax = 174.0f;
