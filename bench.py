@@ -58,9 +58,9 @@ REORDER_KERNELS = 15
 # operations (FFMA + FADD + FMUL + 2 x (FFMA2 + FADD2 + FMUL2) thread
 # instructions); valid only while render.cu's code (comments and whitespace
 # aside) is the code that was profiled.
-NCU = {"render_cu_code_sha256": "4986d06fe36a3d2675b36b88993e9f6a87a1d50866d5a4e7e8c7de1c39a7236c",
-       "bytes_per_launch": 103.716864e6, "fma_pipe_active": 0.6145, "issue_active": 0.6268,
-       "xu_active": 0.1367, "fp32_lane_ops": 14.632718837e9}
+NCU = {"render_cu_code_sha256": "b26ed48b808165f25b91cebb5b2189f88799079aeb5f09a65e078bc64d7d3511",
+       "bytes_per_launch": 103.988736e6, "fma_pipe_active": 0.6125, "issue_active": 0.6250,
+       "xu_active": 0.1359, "fp32_lane_ops": 14.632671605e9}
 
 def issue_rates():
     """Measured lane operations per clock per SM of ex2 / FFMA / packed

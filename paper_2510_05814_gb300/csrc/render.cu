@@ -3,7 +3,10 @@
 // (Sec. III-D), and the fused forward + MSE + backward fit tile.
 //
 // One CTA (4 warps) per tile.  The tile's kernel list is processed in chunks
-// of up to NCH kernels; each chunk is staged in shared memory: the kernel's
+// of up to NCH kernels (256 for the render kernels; 512 for the fused fit
+// tile at T = 16, whose backward re-stages every chunk but the last, so
+// that the longer lists of a fit's later iterations are staged once); each
+// chunk is staged in shared memory: the kernel's
 // prepared record and a ROW MASK, bit r clear only where row r of the tile
 // holds no included pixel.  The row test evaluates the predicate's own FP32
 // value at the row's minimising column (see stage_chunk), so skipping the
@@ -45,6 +48,8 @@
 //   dL/dea_c = E_c, dL/dW_c0 = F_c, dL/dW_c1 = Fy_c, dL/dlogpi = S0.
 #include "smoe_internal.cuh"
 
+#include <type_traits>
+
 namespace smoe {
 
 namespace {
@@ -61,6 +66,9 @@ constexpr int kThreads = kNW * 32;
 #endif
 #ifndef SMOE_NCH
 #define SMOE_NCH 256
+#endif
+#ifndef SMOE_FIT_NCH
+#define SMOE_FIT_NCH 512
 #endif
 #ifndef SMOE_FWD_UNROLL
 #define SMOE_FWD_UNROLL 4
@@ -90,6 +98,11 @@ struct Rec {
     static constexpr int GS = (PI + 1 + 3) & ~3;          // accumulator stride (raw sums)
 };
 
+// Kernels per staged chunk of a tile's list: the render kernels' and the
+// fused fit kernel's (whose backward re-stages every chunk but the last).
+constexpr int default_nch(int T) { return T >= 32 ? 128 : SMOE_NCH; }
+constexpr int fit_nch(int T) { return T == 16 ? SMOE_FIT_NCH : default_nch(T); }
+
 template <int C, int T>
 struct Geom {
     static constexpr int NPX = T * T;
@@ -98,29 +111,40 @@ struct Geom {
     static constexpr int LROW = T / 2;                    // lanes per row (2 px each)
     static constexpr int KSPLIT = BANDS >= kNW ? 1 : kNW / BANDS;
     static constexpr int BPW = BANDS >= kNW ? BANDS / kNW : 1;   // bands per warp
-    static constexpr int NCH = T >= 32 ? 128 : SMOE_NCH;  // kernels per chunk
     static constexpr int PS = 2 * (C + 1);                // floats per pixel pair of state
     static constexpr int RS = (T / 2) * PS + 4;           // floats per row of state (padded)
 };
 
-template <int C, bool LIN, int T>
+// A staged chunk of NC kernels.  The forward's per-warp band lists index a
+// sub-chunk of at most 256 of them in one byte (a longer chunk is walked in
+// sub-chunks: two-byte indices in its inner loop measured 1.6 % slower); the
+// backward groups the whole chunk (its index is read once per group).
+template <int NC>
+struct Chunk {
+    static constexpr int NCH = NC;
+    static constexpr int NSUB = NC < 256 ? NC : 256;
+    using Ord = typename std::conditional<(NC > 256), uint16_t, uint8_t>::type;
+};
+
+template <int C, bool LIN, int T, int NC = default_nch(T)>
 struct Smem {
     using R = Rec<C, LIN>;
     using G = Geom<C, T>;
-    alignas(16) float rec[G::NCH * R::SS];
+    using K = Chunk<NC>;
+    alignas(16) float rec[K::NCH * R::SS];
     alignas(16) float pst[T * G::RS];
     alignas(16) float red[(G::KSPLIT - 1) * (C + 1) * G::NPX + 1];
-    uint32_t mask[G::NCH];
-    int32_t kid[G::NCH];
-    uint8_t flist[kNW][G::NCH];          // per-warp compacted kernel list of a band
-    uint8_t order[G::NCH];               // backward: kernels grouped by row-span centre
+    uint32_t mask[K::NCH];
+    int32_t kid[K::NCH];
+    uint8_t flist[kNW][K::NSUB];         // per-warp compacted kernel list of a band
+    typename K::Ord order[K::NCH];       // backward: kernels grouped by row-span centre
     int bcnt[2 * T], boff[2 * T];        // backward grouping buckets (2T - 1 keys)
     double lsum[kNW];
     long long next;                      // persistent launch: the CTA's next tile
 };
 
-template <int C, bool LIN, int T>
-constexpr size_t smem_bytes() { return sizeof(Smem<C, LIN, T>); }
+template <int C, bool LIN, int T, int NC = default_nch(T)>
+constexpr size_t smem_bytes() { return sizeof(Smem<C, LIN, T, NC>); }
 
 struct TileInfo {
     int b, x0, y0, W, H;
@@ -145,9 +169,9 @@ __device__ __forceinline__ TileInfo tile_info(const Geo &g, const Bufs &w, int64
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
 // Stage kernels [c0, c0 + nc) of the tile's list: records and row masks.
-template <int C, bool LIN, int T>
+template <int C, bool LIN, int T, int NC>
 __device__ __forceinline__ void stage_chunk(const Geo &g, const Bufs &w, const TileInfo &ti,
-                                            int c0, int nc, Smem<C, LIN, T> &sm) {
+                                            int c0, int nc, Smem<C, LIN, T, NC> &sm) {
     using R = Rec<C, LIN>;
     constexpr int Q = R::S / 4;                // float4 per record
     for (int i = threadIdx.x; i < nc * Q; i += kThreads) {
@@ -271,12 +295,13 @@ __device__ __forceinline__ void fwd_pair(const float *r, float y0, float2 x2, fl
 }
 
 // Accumulate D and N_c of one lane's two pixels (row `row`, columns col,
-// col+1 of the tile) over the staged kernels j = j0, j0 + step, ... whose
-// mask meets `band_mask`: the warp first compacts those kernels (ballot),
-// then evaluates them four at a time on two pairs of accumulators.
-template <int C, bool LIN, int T>
+// col+1 of the tile) over the staged kernels s0 + j, j = j0, j0 + step, ...
+// < nc (a sub-chunk of at most 256) whose mask meets `band_mask`: the warp
+// first compacts those kernels (ballot), then evaluates them four at a time
+// on two pairs of accumulators.
+template <int C, bool LIN, int T, int NC>
 __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
-                                         Smem<C, LIN, T> &sm, int nc, int j0, int step,
+                                         Smem<C, LIN, T, NC> &sm, int s0, int nc, int j0, int step,
                                          uint32_t band_mask, int row, int col, float2 &D,
                                          float2 (&N)[C]) {
     using R = Rec<C, LIN>;
@@ -285,12 +310,13 @@ __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
     int cnt = 0;
     for (int base = 0; base < nc; base += 32) {
         const int j = base + lane;
-        const bool hit = j < nc && (j - j0) % step == 0 && j >= j0 && (sm.mask[j] & band_mask);
+        const bool hit = j < nc && (j - j0) % step == 0 && j >= j0 && (sm.mask[s0 + j] & band_mask);
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         if (hit) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
         cnt += __popc(bal);
     }
     __syncwarp();
+    const float *rec = sm.rec + s0 * R::SS;
     const float qmax = g.qmax;
     const float y0 = (float)(ti.y0 + row) + 0.5f;
     const float2 x2 = make_float2((float)(ti.x0 + col) + 0.5f, (float)(ti.x0 + col) + 1.5f);
@@ -301,17 +327,17 @@ __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
 #if SMOE_FWD_UNROLL >= 4
     // four kernels in flight: two pairs of accumulators, each pair fed twice
     for (; i + 3 < cnt; i += 4) {
-        fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
-        fwd_pair<C, LIN>(sm.rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
-        fwd_pair<C, LIN>(sm.rec + lst[i + 2] * R::SS, y0, x2, qmax, D, N);
-        fwd_pair<C, LIN>(sm.rec + lst[i + 3] * R::SS, y0, x2, qmax, D2, N2);
+        fwd_pair<C, LIN>(rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
+        fwd_pair<C, LIN>(rec + lst[i + 2] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(rec + lst[i + 3] * R::SS, y0, x2, qmax, D2, N2);
     }
 #endif
     for (; i + 1 < cnt; i += 2) {
-        fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
-        fwd_pair<C, LIN>(sm.rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
+        fwd_pair<C, LIN>(rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+        fwd_pair<C, LIN>(rec + lst[i + 1] * R::SS, y0, x2, qmax, D2, N2);
     }
-    if (i < cnt) fwd_pair<C, LIN>(sm.rec + lst[i] * R::SS, y0, x2, qmax, D, N);
+    if (i < cnt) fwd_pair<C, LIN>(rec + lst[i] * R::SS, y0, x2, qmax, D, N);
     D = __fadd2_rn(D, D2);
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) N[ch] = __fadd2_rn(N[ch], N2[ch]);
@@ -321,11 +347,12 @@ __device__ __forceinline__ void fwd_band(const Geo &g, const TileInfo &ti,
 // Forward over the whole list.  On return, for every band b the warp owns
 // (bands w, w + 4, ...; T = 8: band 0 summed over the warps), lane l holds
 // D and N_c of pixels (row, col), (row, col + 1) in Dv[bi], Nv[bi].
-template <int C, bool LIN, int T>
+template <int C, bool LIN, int T, int NC>
 __device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
-                                         Smem<C, LIN, T> &sm, float2 (&Dv)[Geom<C, T>::BPW],
+                                         Smem<C, LIN, T, NC> &sm, float2 (&Dv)[Geom<C, T>::BPW],
                                          float2 (&Nv)[Geom<C, T>::BPW][C]) {
     using G = Geom<C, T>;
+    using K = Chunk<NC>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int split = warp % G::KSPLIT;
 #pragma unroll
@@ -334,8 +361,8 @@ __device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const Tile
 #pragma unroll
         for (int ch = 0; ch < C; ++ch) Nv[bi][ch] = f2(0.0f);
     }
-    for (int c0 = 0; c0 < ti.n; c0 += G::NCH) {
-        const int nc = min(G::NCH, ti.n - c0);
+    for (int c0 = 0; c0 < ti.n; c0 += K::NCH) {
+        const int nc = min(K::NCH, ti.n - c0);
         if (c0 > 0) __syncthreads();              // previous chunk fully consumed
         stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
 #pragma unroll
@@ -345,7 +372,9 @@ __device__ __forceinline__ void fwd_tile(const Geo &g, const Bufs &w, const Tile
             lane_pixels<C, T>(bi, row, col);
             const uint32_t bm = (G::BROWS >= 32 ? 0xffffffffu : ((1u << G::BROWS) - 1u))
                                 << (band * G::BROWS);
-            fwd_band<C, LIN, T>(g, ti, sm, nc, split, G::KSPLIT, bm, row, col, Dv[bi], Nv[bi]);
+            for (int s0 = 0; s0 < nc; s0 += K::NSUB)
+                fwd_band<C, LIN, T>(g, ti, sm, s0, min(K::NSUB, nc - s0), split, G::KSPLIT, bm, row,
+                                    col, Dv[bi], Nv[bi]);
         }
     }
     if (G::KSPLIT > 1) {
@@ -503,11 +532,12 @@ struct BwdAcc {
 // (see `group` below): every read of pixel state is a broadcast, lanes
 // whose kernel misses the row contribute zero, and each kernel's sums stay
 // in its two lanes' registers until one float4 atomic per 4 sums at the end.
-template <int C, bool LIN, int T>
+template <int C, bool LIN, int T, int NC>
 __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const TileInfo &ti,
-                                         Smem<C, LIN, T> &sm, bool staged) {
+                                         Smem<C, LIN, T, NC> &sm, bool staged) {
     using R = Rec<C, LIN>;
     using G = Geom<C, T>;
+    using K = Chunk<NC>;
     const float qmax = g.qmax;
     const float2 k2 = f2(kNegHalfLog2e);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -515,9 +545,9 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
     // The chunks last to first: the forward leaves its last chunk staged, so
     // a list longer than one chunk is staged once less (each kernel's sums
     // come from the one chunk that holds it, so the order changes none).
-    const int last = ti.n > 0 ? (ti.n - 1) / G::NCH * G::NCH : 0;
-    for (int c0 = last; c0 >= 0; c0 -= G::NCH) {
-        const int nc = min(G::NCH, ti.n - c0);
+    const int last = ti.n > 0 ? (ti.n - 1) / K::NCH * K::NCH : 0;
+    for (int c0 = last; c0 >= 0; c0 -= K::NCH) {
+        const int nc = min(K::NCH, ti.n - c0);
         __syncthreads();                          // previous users of the chunk are done
         if (!(staged && c0 == last)) stage_chunk<C, LIN, T>(g, w, ti, c0, nc, sm);
         // Group the kernels by the centre of their row span, first + last row
@@ -546,7 +576,7 @@ __device__ __forceinline__ void bwd_tile(const Geo &g, const Bufs &w, const Tile
             const uint32_t m = sm.mask[j];
             if (m) {
                 const int key = (__ffs(m) - 1) + (31 - __clz(m));
-                sm.order[sm.boff[key] + atomicAdd(&sm.bcnt[key], 1)] = (uint8_t)j;
+                sm.order[sm.boff[key] + atomicAdd(&sm.bcnt[key], 1)] = (typename K::Ord)j;
             }
         }
         __syncthreads();
@@ -766,9 +796,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_bwd(const __gri
 // ---------------------------------------------------------------- fused fit tile
 
 // Forward, MSE and backward of global tile t (all threads of the CTA).
-template <int C, bool LIN, int T>
+template <int C, bool LIN, int T, int NC>
 __device__ __forceinline__ void fit_tile_body(const Geo &g, const Bufs &w, int64_t t,
-                                              Smem<C, LIN, T> &sm, double *loss, int32_t hist,
+                                              Smem<C, LIN, T, NC> &sm, double *loss, int32_t hist,
                                               const int32_t *__restrict__ step) {
     using G = Geom<C, T>;
     const TileInfo ti = tile_info(g, w, t);
@@ -848,7 +878,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_fit_tile(const __grid_
                                                           const int32_t *__restrict__ step) {
     if (status_bad(w.status)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
+    Smem<C, LIN, T, fit_nch(T)> &sm = *reinterpret_cast<Smem<C, LIN, T, fit_nch(T)> *>(smem_raw);
     fit_tile_body<C, LIN, T>(g, w, blockIdx.x, sm, loss, hist, step);
 }
 
@@ -860,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
                           const int32_t *__restrict__ step) {
     if (status_bad(w.status)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<C, LIN, T> &sm = *reinterpret_cast<Smem<C, LIN, T> *>(smem_raw);
+    Smem<C, LIN, T, fit_nch(T)> &sm = *reinterpret_cast<Smem<C, LIN, T, fit_nch(T)> *>(smem_raw);
     for (;;) {
         if (threadIdx.x == 0) sm.next = (long long)atomicAdd(w.work, 1u);
         __syncthreads();
@@ -919,6 +949,7 @@ cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y,
     const unsigned grid = (unsigned)g.tiles_total;
     if (grid == 0) return cudaSuccess;
     constexpr size_t smem = smem_bytes<C, LIN, T>();
+    constexpr size_t smem_fit = smem_bytes<C, LIN, T, fit_nch(T)>();
     static bool a0 = false, a1 = false, a2 = false;
     cudaError_t e;
     if (which == 0) {
@@ -928,8 +959,8 @@ cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y,
         if ((e = smem_attr(k_render_bwd<C, LIN, T>, smem, a1)) != cudaSuccess) return e;
         k_render_bwd<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, y, inv_d, gy, target);
     } else if (which == 2) {
-        if ((e = smem_attr(k_fit_tile<C, LIN, T>, smem, a2)) != cudaSuccess) return e;
-        k_fit_tile<C, LIN, T><<<grid, kThreads, smem, st>>>(g, w, loss, hist, step);
+        if ((e = smem_attr(k_fit_tile<C, LIN, T>, smem_fit, a2)) != cudaSuccess) return e;
+        k_fit_tile<C, LIN, T><<<grid, kThreads, smem_fit, st>>>(g, w, loss, hist, step);
     } else if (which == 4) {
         static bool a4 = false;
         if ((e = smem_attr(k_render_mean<C, LIN, T>, smem, a4)) != cudaSuccess) return e;
@@ -937,20 +968,20 @@ cudaError_t dispatch_one(const Geo &g, const Bufs &w, int which, const float *y,
     } else {
         static bool a3 = false;
         static int resident = 0;
-        if ((e = smem_attr(k_fit_tile_persistent<C, LIN, T>, smem, a3)) != cudaSuccess) return e;
+        if ((e = smem_attr(k_fit_tile_persistent<C, LIN, T>, smem_fit, a3)) != cudaSuccess) return e;
         if (!resident) {
             int dev = 0, sms = 0, per_sm = 0;
             if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
             if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
                 return e;
             if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                     &per_sm, k_fit_tile_persistent<C, LIN, T>, kThreads, smem)) != cudaSuccess)
+                     &per_sm, k_fit_tile_persistent<C, LIN, T>, kThreads, smem_fit)) != cudaSuccess)
                 return e;
             resident = sms * (per_sm > 0 ? per_sm : 1);
         }
         if ((e = cudaMemsetAsync(w.work, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
         const unsigned pg = grid < (unsigned)resident ? grid : (unsigned)resident;
-        k_fit_tile_persistent<C, LIN, T><<<pg, kThreads, smem, st>>>(g, w, loss, hist, step);
+        k_fit_tile_persistent<C, LIN, T><<<pg, kThreads, smem_fit, st>>>(g, w, loss, hist, step);
     }
     return cudaGetLastError();
 }

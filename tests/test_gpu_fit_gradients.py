@@ -193,3 +193,24 @@ def test_fit_gradients_degenerate_kernels(C, linear, tile):
     compare(g, ref, terms, f"degenerate C={C}")
     nan_k = 9                                  # mu = (nan, 0.5): listed in no tile
     assert all(float(x[nan_k].abs().sum()) == 0.0 for x in g.tensors())
+
+
+@pytest.mark.parametrize("mode", ["grid", "persistent", "deterministic"])
+def test_fit_gradients_long_lists(mode):
+    """Tile lists of 505 to 810 kernels: the fused kernel stages a list in
+    chunks and walks a chunk in sub-chunks of 256, so its forward and its
+    backward cross both boundaries.  Thin kernels keep the count included at
+    a pixel near 350 while their square boxes list them almost everywhere;
+    the gradients match the oracle's at the gradient bar."""
+    W, H = 64, 48
+    p = rand_case(43, W, H, 3, 900, True, sig=(1.0, 12.0), span=(0.05, 0.95))
+    t = synth.polygon_image(W, H, 3, 5, 343, texture_amp=0.1)
+    off, _ = om.bin_tiles(om.Model(W, H, 3, p.mu, p.chol, p.ea, p.eW, tile=16))
+    lens = np.diff(off)
+    assert lens.min() > 256 and lens.max() > 512, (lens.min(), lens.max())
+    fb = FitBatch([torch.tensor(t, device="cuda")], [api.SMoEParams.from_numpy(p)], 2, lr=LR,
+                  tile=16, persistent=mode == "persistent", deterministic=mode == "deterministic")
+    g = fb.gradients()[0]
+    assert fb.status_code() == 0
+    ref, terms = oracle_grads(p, t, 16)
+    compare(g, ref, terms, f"long lists ({mode})")
