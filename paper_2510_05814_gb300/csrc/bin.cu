@@ -711,6 +711,10 @@ __global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(const __grid
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= n_tiles) return;
+    // queued kernels appended to this list: each is a block of its own and
+    // they span the kernel order, so the block merge below would not apply
+    // (the list takes the full sort)
+    int n_app = 0;
     if (w.huge) {
         // the queued (huge) kernels that hold this tile go after the slots the
         // scatter filled, up to the tile's end, each as its own block
@@ -734,6 +738,7 @@ __global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(const __grid
                 const unsigned bal = __ballot_sync(0xffffffffu, cov);
                 if (cov) w.pair_tmp[at + __popc(bal & ((1u << lane) - 1u))] = k | kBlockHead;
                 at += __popc(bal);
+                n_app += __popc(bal);
             }
             __syncwarp();
         }
@@ -751,10 +756,10 @@ __global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(const __grid
     } else if (n <= 128) {
         warp_sort_list<4>(w, start, n, lane);
     } else if (n <= 256) {
-        if (!warp_merge_runs<8>(w, start, n, lane, runs[threadIdx.x >> 5]))
+        if (n_app > 0 || !warp_merge_runs<8>(w, start, n, lane, runs[threadIdx.x >> 5]))
             warp_sort_list<8>(w, start, n, lane);
     } else if (n <= 512) {
-        if (!warp_merge_runs<16>(w, start, n, lane, runs[threadIdx.x >> 5]))
+        if (n_app > 0 || !warp_merge_runs<16>(w, start, n, lane, runs[threadIdx.x >> 5]))
             warp_sort_list<16>(w, start, n, lane);
     } else if (lane == 0) {
         w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
