@@ -704,45 +704,73 @@ __device__ __forceinline__ bool warp_merge_runs(const Bufs &w, int64_t start, in
 // queued for k_segsort_long.
 constexpr int kShortSortThreads = 128;
 
-__global__ void __launch_bounds__(kShortSortThreads) k_segsort_warp(const __grid_constant__ Geo g,
-                                                                    int64_t n_tiles, Bufs w) {
-    __shared__ WarpRuns runs[kShortSortThreads / 32];
+// The sort kernel's CTAs take 8 tiles, so that a pass over the queue of
+// huge kernels is staged in shared memory once for 8 tiles.
+#ifndef SMOE_SEGSORT_THREADS
+#define SMOE_SEGSORT_THREADS 256
+#endif
+constexpr int kSegThreads = SMOE_SEGSORT_THREADS;
+constexpr int kHugeStage = kSegThreads;          // queued kernels staged per pass
+
+__global__ void __launch_bounds__(kSegThreads) k_segsort_warp(const __grid_constant__ Geo g,
+                                                              int64_t n_tiles, Bufs w) {
+    __shared__ WarpRuns runs[kSegThreads / 32];
+    __shared__ int4 hq_rect[kHugeStage];
+    __shared__ int32_t hq_k[kHugeStage], hq_b[kHugeStage];
     if (status_bad(w.status)) return;
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (t >= n_tiles) return;
+    const bool tile_ok = t < n_tiles;
     // queued kernels appended to this list: each is a block of its own and
     // they span the kernel order, so the block merge below would not apply
     // (the list takes the full sort)
     int n_app = 0;
-    if (w.huge) {
+    const int nh = w.huge ? *w.n_huge : 0;         // the same for every thread
+    if (nh > 0) {
         // the queued (huge) kernels that hold this tile go after the slots the
-        // scatter filled, up to the tile's end, each as its own block
-        const int nh = *w.n_huge;
-        if (nh > 0) {
-            const int b = img_by_tile(g, t);
+        // scatter filled, up to the tile's end, each as its own block; the
+        // queue passes through shared memory a CTA-wide pass at a time
+        int b = -1, tx = 0, ty = 0;
+        int32_t at = 0;
+        if (tile_ok) {
+            b = img_by_tile(g, t);
             const ImgDev &im = img_of(g, b);
             const int64_t local = t - im.t_off;
-            const int tx = (int)(local % im.tiles_x), ty = (int)(local / im.tiles_x);
-            int32_t at = w.cursor[t];
-            for (int i0 = 0; i0 < nh; i0 += 32) {
-                const int i = i0 + lane;
-                int32_t k = 0;
-                bool cov = false;
-                if (i < nh) {
-                    k = w.huge[i];
-                    const int4 r = w.rect[k];
-                    cov = img_by_kernel(g, k) == b && r.x <= tx && tx <= r.z && r.y <= ty &&
-                          ty <= r.w;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, cov);
-                if (cov) w.pair_tmp[at + __popc(bal & ((1u << lane) - 1u))] = k | kBlockHead;
-                at += __popc(bal);
-                n_app += __popc(bal);
-            }
-            __syncwarp();
+            tx = (int)(local % im.tiles_x);
+            ty = (int)(local / im.tiles_x);
+            at = w.cursor[t];
         }
+        for (int c0 = 0; c0 < nh; c0 += kHugeStage) {
+            __syncthreads();                           // the previous pass is read
+            const int i = c0 + (int)threadIdx.x;
+            if (i < nh) {
+                const int32_t k = w.huge[i];
+                hq_k[threadIdx.x] = k;
+                hq_rect[threadIdx.x] = w.rect[k];
+                hq_b[threadIdx.x] = img_by_kernel(g, k);
+            }
+            __syncthreads();
+            const int m = min(kHugeStage, nh - c0);
+            if (tile_ok) {
+                for (int j0 = 0; j0 < m; j0 += 32) {
+                    const int j = j0 + lane;
+                    int32_t k = 0;
+                    bool cov = false;
+                    if (j < m) {
+                        const int4 r = hq_rect[j];
+                        k = hq_k[j];
+                        cov = hq_b[j] == b && r.x <= tx && tx <= r.z && r.y <= ty && ty <= r.w;
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, cov);
+                    if (cov) w.pair_tmp[at + __popc(bal & ((1u << lane) - 1u))] = k | kBlockHead;
+                    at += __popc(bal);
+                    n_app += __popc(bal);
+                }
+            }
+        }
+        __syncwarp();
     }
+    if (!tile_ok) return;
     const int64_t start = w.tile_off[t];
     const int n = (int)(w.tile_off[t + 1] - start);
     if (n <= 1) {
@@ -917,8 +945,8 @@ cudaError_t launch_bin(const Geo &g, const Bufs &w, cudaStream_t st) {
 cudaError_t launch_sort_lists(const Geo &g, const Bufs &w, cudaStream_t st) {
     const int64_t n = g.tiles_total;
     if (n > 0) {
-        constexpr int wpb = kShortSortThreads / 32;
-        k_segsort_warp<<<(unsigned)((n + wpb - 1) / wpb), kShortSortThreads, 0, st>>>(g, n, w);
+        constexpr int wpb = kSegThreads / 32;
+        k_segsort_warp<<<(unsigned)((n + wpb - 1) / wpb), kSegThreads, 0, st>>>(g, n, w);
         const int64_t gl = n < kLongGrid ? n : kLongGrid;
         k_segsort_long<<<(unsigned)gl, kSortThreads, 0, st>>>(g, w);
     }
