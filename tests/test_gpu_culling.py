@@ -247,3 +247,35 @@ def test_huge_rectangles_in_a_batch_stay_in_their_image():
         for x, y in zip(both.params_of(b).tensors(), one.params_of(0).tensors()):
             assert torch.equal(x, y)
         np.testing.assert_allclose(both.losses()[b], one.losses()[0], rtol=1e-12)
+
+
+@pytest.mark.parametrize("n_huge", [40, 150])
+def test_appended_huge_ids_in_long_lists_are_bit_exact(n_huge):
+    """Lists of 129 to 512 ids that also carry queued huge kernels: the
+    scatter's blocks are merged, the appended ids sorted and the two runs
+    merged by rank (up to 128 appended ids; 150 take the full sort).  The
+    lists are the oracle's, bit for bit."""
+    W = H = 768                                            # 48 x 48 tiles
+    rng = np.random.default_rng(500 + n_huge)
+    K = 30000
+    mu = rng.uniform(0.0, 1.0, (K, 2))
+    s = rng.uniform(6.0, 12.0, K)
+    chol = np.stack([1 / s, rng.normal(0, 0.02, K), 1 / s], 1)
+    # the first n_huge kernels cover every tile: a zero Cholesky entry, or a
+    # stripe across the raster, at scattered positions in the kernel order
+    idx = rng.choice(K, n_huge, replace=False)
+    for i, k in enumerate(idx):
+        chol[k] = (0.0, 0.3, 0.3) if i % 2 else (1e-5, 0.0, 1e-5)
+    p = synth.Params(mu.astype(np.float32), chol.astype(np.float32),
+                     rng.uniform(0, 1, (K, 3)).astype(np.float32),
+                     rng.normal(0, 0.02, (K, 3, 2)).astype(np.float32))
+    m = om.Model(W, H, 3, p.mu, p.chol, p.ea, p.eW, tile=16)
+    ref_off, ref_pk = om.bin_tiles(m)
+    lens = np.diff(ref_off)
+    assert (lens > 128).mean() > 0.5 and lens.max() <= 512 + n_huge, (lens.min(), lens.max())
+    assert all(om.rect(m, int(k))[1] > 1024 for k in idx)
+    params = api.SMoEParams.from_numpy(p)
+    r = api.Rasterizer(api.RasterDesc(W, H, 3, 16, True), params.K).bin(params)
+    off, pk = r.lists()
+    np.testing.assert_array_equal(off.astype(np.int64), ref_off)
+    np.testing.assert_array_equal(pk, ref_pk)
