@@ -46,9 +46,10 @@ MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measu
 FP32_OPS_PER_PAIR = 67
 # PSNR the fit-to-PSNR leg times the 2048^2 fit to.
 FIT_TARGET_DB = 50.0
-# Kernels launched by one fit step: binning (bbox, scan reduce/top/down,
-# scatter, warp sort, long-list sort), the fused tile kernel, fused Adam.
-KERNELS_PER_STEP = 9
+# Kernels launched by one fit step: binning (bbox, huge-box cover, scan
+# reduce/top/down, scatter, warp sort, long-list sort), the fused tile
+# kernel, fused Adam.
+KERNELS_PER_STEP = 10
 # The fit re-sorts its kernels spatially every this many steps (FitBatch
 # reorder_every; smoe_fit_reorder, 15 kernels); the timed steps include it.
 REORDER_EVERY = 25
@@ -499,8 +500,12 @@ def run_serve(args):
     import torch
     from paper_2510_05814_gb300 import build, serve
     build.build()
+    sizes = None
+    if args.fit_size:
+        W, H = (int(v) for v in args.fit_size.lower().split("x"))
+        sizes = [(W, H)]
     reqs = serve.poisson_workload(args.fits, args.renders, args.rate, iters=args.iters,
-                                  sizes=None, mm_models=args.mm_models)
+                                  sizes=sizes, mm_models=args.mm_models)
     srv = serve.Server(args.budget_gb * (1 << 30), chunk=25,
                        max_pixels=int(args.max_mpx * 1e6) if args.max_mpx else None)
     t0 = time.perf_counter()
@@ -518,6 +523,7 @@ def run_serve(args):
         "metric": "serving: fit/render request latency p50/p99 and throughput, continuous "
                   "batching vs one request at a time", "mode": "serve",
         "mm_models_per_denoising_request": args.mm_models,
+        "fit_size": args.fit_size or "ragged 128x96 .. 1920x1080",
         "max_mpx_in_flight": args.max_mpx or None,
         "requests": len(reqs), "fits": len(fits), "rate_per_s": args.rate, "iters": args.iters,
         "batched": {"wall_s": t_b, "req_per_s": len(reqs) / t_b,
@@ -726,6 +732,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--max-mpx", type=float, default=16.0,
                     help="serve: cap on megapixels (x models) in flight (0: HBM budget only)")
+    ap.add_argument("--fit-size", default=None,
+                    help="serve: every fit request at this WxH (e.g. 2048x2048) instead of the "
+                         "ragged sizes")
     ap.add_argument("--mm-models", type=int, default=4,
                     help="serve: MM-RSMoE models per denoising request")
     args = ap.parse_args()
@@ -892,7 +901,7 @@ def run_fit(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     # The step as FitBatch.run(graph_iters=...) runs it: one CUDA-graph replay
-    # of a whole fit iteration (its 9 kernels), L2 flushed before each step.
+    # of a whole fit iteration (its 10 kernels), L2 flushed before each step.
     graph = fb.capture(1)
     graph.replay()                              # one untimed replay
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
