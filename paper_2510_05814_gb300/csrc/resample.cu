@@ -9,7 +9,8 @@
 // the points of one tile next to each other, and one thread per point then
 // walks its tile's kernel list.  Neighbouring threads of a warp mostly share
 // a tile, so their reads of a kernel's prepared record are the same address
-// (one transaction for the warp) and the records stay in L2.
+// (one transaction for the warp) and the records stay in L2; such a warp
+// first culls the list against its points' rows (k_render_points).
 #include <cmath>
 
 #include "smoe_internal.cuh"
@@ -68,8 +69,43 @@ __global__ void k_pt_scatter(int64_t n, const int32_t *__restrict__ pt_tile,
     order[base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;   // cursor starts at off[t]
 }
 
+// One kernel's contribution to a point (p): the predicate's own FP32
+// operations, then pi exp(-q/2) and the expert values.
+template <int C, bool LIN>
+__device__ __forceinline__ void point_pair(const float *r, float2 p, float qmax, float &D,
+                                           float (&N)[C]) {
+    constexpr int E = LIN ? 3 : 1;
+    const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
+    const float c = __ldg(r + 4), lp = __ldg(r + 5);
+    const float dy = __fsub_rn(p.y, r0.y);
+    const float z1 = __fmul_rn(c, dy);
+    const float u = __fmul_rn(z1, z1);
+    if (!(u <= qmax)) return;                // q = fma(z0, z0, u) >= u: not included
+    const float dx = __fsub_rn(p.x, r0.x);
+    const float tb = __fmul_rn(r0.w, dy);
+    float z0;
+    const float qv = q_of(r0.z, dx, tb, u, z0);
+    if (!(qv <= qmax)) return;
+    const float ev = ex2(__fmaf_rn(qv, kNegHalfLog2e, lp));       // pi exp(-q/2)
+    D += ev;
+#pragma unroll
+    for (int ch = 0; ch < C; ++ch) {
+        float m = __ldg(r + 7 + ch * E);
+        if (LIN) m = __fmaf_rn(__ldg(r + 7 + ch * E + 1), dx,
+                               __fmaf_rn(__ldg(r + 7 + ch * E + 2), dy, m));
+        N[ch] = __fmaf_rn(ev, m, N[ch]);
+    }
+}
+
 // One thread per sorted in-image point: D = sum e_k, N_c = sum e_k m_kc over
 // the tile's list in ascending kernel order, y_c = N_c / D (0 where D = 0).
+// A warp whose points share one tile first culls the list 32 kernels at a
+// time against its points' rows: a kernel passes when some point of the
+// warp has u = (c dy)^2 <= q_max, computed with the predicate's own
+// operations at the warp's lowest and highest point (u is monotone in the
+// point's y on each side of the centre; a centre between them passes).  A
+// culled kernel includes none of the warp's points, so the sums, taken over
+// the passing kernels in list order, are the per-point walk's bit for bit.
 template <int C, bool LIN>
 __global__ void __launch_bounds__(kPtThreads) k_render_points(
     int64_t n, const int64_t *__restrict__ n_in, const float2 *__restrict__ xy,
@@ -77,40 +113,55 @@ __global__ void __launch_bounds__(kPtThreads) k_render_points(
     const int32_t *__restrict__ tile_off, const int32_t *__restrict__ pair_k,
     const float *__restrict__ rec, int S, float qmax, int rbf, float *__restrict__ y,
     float *__restrict__ inv_d, const int32_t *status) {
-    constexpr int E = LIN ? 3 : 1;
+    const unsigned full = 0xffffffffu;
     if (status_bad(status)) return;
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= *n_in) return;
-    const int32_t i = order[j];
-    const int32_t t = pt_tile[i];
-    const float2 p = xy[i];
+    const int64_t nin = *n_in;
+    if (j - (threadIdx.x & 31) >= nin) return;          // the whole warp is past the end
+    const bool active = j < nin;
+    const int lane = threadIdx.x & 31;
+    const int32_t i = active ? order[j] : 0;
+    const int32_t t = active ? pt_tile[i] : -1;
+    const float2 p = active ? xy[i] : make_float2(0.0f, 0.0f);
     float D = 0.0f, N[C];
 #pragma unroll
     for (int ch = 0; ch < C; ++ch) N[ch] = 0.0f;
-    const int32_t e = tile_off[t + 1];
-    for (int32_t q = tile_off[t]; q < e; ++q) {
-        const float *r = rec + (int64_t)pair_k[q] * S;
-        const float4 r0 = __ldg(reinterpret_cast<const float4 *>(r));
-        const float c = __ldg(r + 4), lp = __ldg(r + 5);
-        const float dy = __fsub_rn(p.y, r0.y);
-        const float z1 = __fmul_rn(c, dy);
-        const float u = __fmul_rn(z1, z1);
-        if (!(u <= qmax)) continue;          // q = fma(z0, z0, u) >= u: not included
-        const float dx = __fsub_rn(p.x, r0.x);
-        const float tb = __fmul_rn(r0.w, dy);
-        float z0;
-        const float qv = q_of(r0.z, dx, tb, u, z0);
-        if (!(qv <= qmax)) continue;
-        const float ev = ex2(__fmaf_rn(qv, kNegHalfLog2e, lp));     // pi exp(-q/2)
-        D += ev;
+    const int32_t t0 = __shfl_sync(full, t, 0);         // lane 0 is active
+    if (__all_sync(full, !active || t == t0)) {
+        float ylo = active ? p.y : INFINITY, yhi = active ? p.y : -INFINITY;
 #pragma unroll
-        for (int ch = 0; ch < C; ++ch) {
-            float m = __ldg(r + 7 + ch * E);
-            if (LIN) m = __fmaf_rn(__ldg(r + 7 + ch * E + 1), dx,
-                                   __fmaf_rn(__ldg(r + 7 + ch * E + 2), dy, m));
-            N[ch] = __fmaf_rn(ev, m, N[ch]);
+        for (int o = 16; o > 0; o >>= 1) {
+            ylo = fminf(ylo, __shfl_xor_sync(full, ylo, o));
+            yhi = fmaxf(yhi, __shfl_xor_sync(full, yhi, o));
         }
+        const int32_t s0 = tile_off[t0], e0 = tile_off[t0 + 1];
+        for (int32_t q0 = s0; q0 < e0; q0 += 32) {
+            const int32_t q = q0 + lane;
+            int32_t kid = 0;
+            bool pass = false;
+            if (q < e0) {
+                kid = pair_k[q];
+                const float *r = rec + (int64_t)kid * S;
+                const float my = __ldg(r + 1), c = __ldg(r + 4);
+                const float zl = __fmul_rn(c, __fsub_rn(ylo, my));
+                const float zh = __fmul_rn(c, __fsub_rn(yhi, my));
+                pass = (my >= ylo && my <= yhi) || __fmul_rn(zl, zl) <= qmax ||
+                       __fmul_rn(zh, zh) <= qmax;
+            }
+            unsigned bal = __ballot_sync(full, pass);
+            while (bal) {
+                const int l = __ffs(bal) - 1;
+                bal &= bal - 1;
+                const int32_t k = __shfl_sync(full, kid, l);
+                if (active) point_pair<C, LIN>(rec + (int64_t)k * S, p, qmax, D, N);
+            }
+        }
+    } else if (active) {
+        const int32_t e = tile_off[t + 1];
+        for (int32_t q = tile_off[t]; q < e; ++q)
+            point_pair<C, LIN>(rec + (int64_t)pair_k[q] * S, p, qmax, D, N);
     }
+    if (!active) return;
     const float inv = D > 0.0f ? 1.0f / D : 0.0f;
     const float sc = rbf ? 1.0f : inv;                // Eq. 1 does not normalise
 #pragma unroll
