@@ -182,3 +182,28 @@ def test_ten_times_magnification_of_the_2048_model_sampled():
     m = om.Model(W, H, C, P.mu[ids], P.chol[ids], P.ea[ids], P.eW[ids], tile=16)
     ref, _, absm = om.render_points(m, pts[sel], with_scale=True)
     assert np.all(np.abs(got[:, sel] - ref) <= RTOL_Y * np.maximum(np.abs(ref), absm))
+
+
+@pytest.mark.parametrize("C,linear", [(3, True), (1, False)])
+def test_warp_row_culling_is_bit_identical_to_the_point_walk(C, linear):
+    """The same sparse points rendered alone (their warps span several tiles
+    and walk the lists point by point) and among a dense jittered raster
+    (their warps share a tile and cull the list against their rows first):
+    the values are equal bit for bit, and match the oracle."""
+    W, H, T = 96, 80, 16
+    p = rand_params(77 + C, C, 400, linear, sig=(1.0, 9.0))
+    params = api.SMoEParams.from_numpy(p)
+    rng = np.random.default_rng(78)
+    sparse = np.stack([rng.uniform(0, W, 300), rng.uniform(0, H, 300)], 1).astype(np.float32)
+    g = (np.arange(W * 4) + 0.5) / 4.0
+    gy = (np.arange(H * 4) + 0.5) / 4.0
+    dense = np.stack(np.meshgrid(g, gy), -1).reshape(-1, 2)
+    dense = (dense + rng.uniform(-0.1, 0.1, dense.shape)).astype(np.float32)
+    alone, _, _ = api.render_points(params, W, H, torch.tensor(sparse, device="cuda"), tile=T)
+    mixed, _, _ = api.render_points(params, W, H,
+                                    torch.tensor(np.concatenate([dense, sparse]), device="cuda"),
+                                    tile=T)
+    assert torch.equal(mixed[:, dense.shape[0]:], alone)
+    m = om.Model(W, H, C, p.mu, p.chol, p.ea, p.eW, tile=T)
+    ref, _, absm = om.render_points(m, sparse, with_scale=True)
+    assert np.all(np.abs(alone.cpu().numpy() - ref) <= RTOL_Y * np.maximum(np.abs(ref), absm))
