@@ -105,7 +105,12 @@ __global__ void k_adam_coefs(const __grid_constant__ Geo g, const int32_t *step,
 // elements, so every global access is coalesced.  The last CTA to finish
 // advances every running image's step counter and forms the coefficients of
 // the next step.
-constexpr int kAdamThreads = 256;
+// Kernels per CTA of the Adam launches: 128 measured 4 % faster than 256
+// on the 2048^2 fit (38.9 against 40.5 us; 512 spills).
+#ifndef SMOE_ADAM_THREADS
+#define SMOE_ADAM_THREADS 128
+#endif
+constexpr int kAdamThreads = SMOE_ADAM_THREADS;
 
 // Adam on one parameter group of a CTA's kernels (N values per kernel):
 // gradients in shared memory (gs[e], e = t N + j for kernel k0 + t), `img`
