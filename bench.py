@@ -573,14 +573,17 @@ def psnr_of_mse(mse):
     return 10.0 * np.log10(1.0 / np.maximum(mse, 1e-300))
 
 
-def fit_to_psnr_leg(wl, params0, iters, target_db, chunk=25):
+def fit_to_psnr_leg(wl, params0, iters, target_db, chunk=25, late_n=20):
     """A whole fit of the 2048^2 workload from its initial kernels, the way a
     caller runs it (FitBatch.run with CUDA-graph replays of `chunk`
     iterations and the spatial re-sort every 25): CUDA events after every
     chunk give the fit's device time at each point of its loss history
     (the MSE of every iteration, before its update).  Returns the wall time,
     the time to the first iteration whose MSE reaches `target_db` PSNR, and
-    the PSNR of the final model rendered and clamped to [0, 1]."""
+    the PSNR of the final model rendered and clamped to [0, 1].  Then, outside
+    the fit's timing, `late_n` more iterations run phase by phase (L2 flushed
+    before each): the step's phases at the end of a fit, where the kernels
+    have stretched and the lists grown."""
     import numpy as np
     import torch
     from paper_2510_05814_gb300 import api, synth
@@ -589,8 +592,9 @@ def fit_to_psnr_leg(wl, params0, iters, target_db, chunk=25):
     tgt = torch.tensor(wl.target, device="cuda")
     cap = None
     for _attempt in range(4):
-        fb = FitBatch([tgt], [params0.clone()], iters, lr=synth.fit_rates(W, H), tile=wl.tile,
-                      qmax=wl.qmax, hist=iters, reorder_every=REORDER_EVERY, pair_cap=cap)
+        fb = FitBatch([tgt], [params0.clone()], iters + late_n, lr=synth.fit_rates(W, H),
+                      tile=wl.tile, qmax=wl.qmax, hist=iters + late_n,
+                      reorder_every=REORDER_EVERY, pair_cap=cap)
         fb.capture(chunk)
         n_chunks = iters // chunk
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_chunks + 1)]
@@ -615,13 +619,33 @@ def fit_to_psnr_leg(wl, params0, iters, target_db, chunk=25):
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     api.smoe_sq_error(y, tgt, out, clamp=True)
     final = float(psnr_of_mse(out.item() / y.numel()))
+    late = None
+    if late_n:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        pev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(late_n)]
+        for e in pev:
+            flush.zero_()
+            e[0].record()
+            fb.phase(0)
+            e[1].record()
+            fb.phase(1)
+            e[2].record()
+            fb.phase(2)
+            e[3].record()
+        torch.cuda.synchronize()
+        assert fb.status_code() == 0
+        med = lambda a, b: statistics.median(e[a].elapsed_time(e[b]) for e in pev)
+        late = {"after_iter": n_chunks * chunk, "bin": med(0, 1), "fused_tiles": med(1, 2),
+                "adam": med(2, 3), "steps": late_n,
+                "how": "the fit's next iterations, launched phase by phase (no graph), CUDA "
+                       "events between the phases, L2 flushed before each; median"}
     marks = [0, 100, 300, 1000, 2000, 5000, n_chunks * chunk - 1]
     return {"iters": n_chunks * chunk, "lr": list(synth.fit_rates(W, H)),
             "device_s": float(t_at[-1]), "wall_s": wall,
             "iters_per_s": n_chunks * chunk / float(t_at[-1]),
             "target_psnr_db": target_db, "s_to_target": t_hit,
             "iters_to_target": int(hit[0]) + 1 if len(hit) else None,
-            "psnr_final_db": final, "psnr_max_db": float(ps.max()),
+            "psnr_final_db": final, "psnr_max_db": float(ps.max()), "late_phases_ms": late,
             "uncovered_px": float((inv == 0).float().mean()),
             "psnr_db_at": {int(i): round(float(ps[i]), 3) for i in marks if i < len(ps)},
             "how": f"fresh fit from the initial kernels, graph replays of {chunk} iterations, "
