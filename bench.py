@@ -44,6 +44,10 @@ MUFU_PER_CLK_PER_SM = 32          # ex2 lanes per clock per SM if the live measu
 # experts: 19 in the forward and 48 in the backward (the per-pair count of the
 # method's formulas, Eqs. 2-5 and their chain rule).
 FP32_OPS_PER_PAIR = 67
+# The server's cap on megapixels (image pixels x models) in flight: 8 / 16 /
+# 32 / 64 measured 12.7 / 14.4 / 15.5 / 15.9 requests/s with p99 5.0 / 4.6 /
+# 4.2 / 4.3 s on the serving workload (p50 3.2 / 2.4 / 3.2 / 3.9 s).
+SERVE_MAX_MPX = 32.0
 # PSNR the fit-to-PSNR leg times the 2048^2 fit to.
 FIT_TARGET_DB = 50.0
 # Kernels launched by one fit step: binning (bbox, huge-box cover, scan
@@ -754,7 +758,7 @@ def main():
     ap.add_argument("--renders", type=int, default=40)
     ap.add_argument("--rate", type=float, default=50.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
-    ap.add_argument("--max-mpx", type=float, default=16.0,
+    ap.add_argument("--max-mpx", type=float, default=SERVE_MAX_MPX,
                     help="serve: cap on megapixels (x models) in flight (0: HBM budget only)")
     ap.add_argument("--fit-size", default=None,
                     help="serve: every fit request at this WxH (e.g. 2048x2048) instead of the "
@@ -784,12 +788,12 @@ def serving_leg(rimgs, n_fit, iters, mm_models=4, rate=50.0):
     stream: n_fit fit requests on the batched leg's ragged images (half of
     them denoising, N(0, 0.05) added, as MM-RSMoE with mm_models models) and
     as many render requests at 1-4x; the server admits by a 150 GB budget and
-    16 Mpx in flight (paper_2510_05814_gb300.serve)."""
+    SERVE_MAX_MPX megapixels in flight (paper_2510_05814_gb300.serve)."""
     import numpy as np
     from paper_2510_05814_gb300 import serve
     reqs = serve.poisson_workload(n_fit, n_fit, rate, iters=iters, mm_models=mm_models,
                                   images=[t for t, _ in rimgs[:n_fit]])
-    srv = serve.Server(150 * (1 << 30), chunk=25, max_pixels=int(16e6))
+    srv = serve.Server(150 * (1 << 30), chunk=25, max_pixels=int(SERVE_MAX_MPX * 1e6))
     t0 = time.perf_counter()
     res_b = srv.run(reqs, realtime=True)
     t_b = time.perf_counter() - t0
