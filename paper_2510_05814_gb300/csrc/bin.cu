@@ -790,7 +790,8 @@ __global__ void __launch_bounds__(kSegThreads) k_segsort_warp(const __grid_const
         if (n_app > 0 || !warp_merge_runs<16>(w, start, n, lane, runs[threadIdx.x >> 5]))
             warp_sort_list<16>(w, start, n, lane);
     } else if (lane == 0) {
-        w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t;
+        // the top bit marks a list that carries appended queued kernels
+        w.long_q[atomicAdd(w.n_long, 1)] = (int32_t)t | (n_app > 0 ? kBlockHead : 0);
     }
 }
 
@@ -810,17 +811,18 @@ __global__ void __launch_bounds__(kSortThreads) k_segsort_long(const __grid_cons
         const int q = q0 + warp * gridDim.x;
         bool ok = false;
         if (q < n_long) {
-            const int64_t t = w.long_q[q];
+            const int32_t e = w.long_q[q];
+            const int64_t t = e & kIdMask;
             const int64_t start = w.tile_off[t];
             const int n = (int)(w.tile_off[t + 1] - start);
-            ok = n <= 1024 && warp_merge_runs<32>(w, start, n, lane, runs[warp]);
+            ok = e >= 0 && n <= 1024 && warp_merge_runs<32>(w, start, n, lane, runs[warp]);
         }
         if (lane == 0) merged[warp] = ok;
         __syncthreads();
         for (int j = 0; j < kWarps; ++j) {
             const int qq = q0 + j * gridDim.x;
             if (qq >= n_long) break;
-            if (!merged[j]) segsort_tile(g, w, w.long_q[qq], s);
+            if (!merged[j]) segsort_tile(g, w, w.long_q[qq] & kIdMask, s);
             __syncthreads();
         }
     }
